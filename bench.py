@@ -1,0 +1,345 @@
+"""Benchmark: max-flow solve of the 256x256x128 6-connected grid (8,388,610 vertices, 50,331,648 CSR
+slots) on one GB300 through libmf's C-ABI.
+
+One step = one complete mf_solve: reset from the capacities, phase 1 (maximum preflow: synchronous
+discharge rounds + BFS global relabels), phase 2 (excess returned to s), cut BFS, per-slot flow and cut
+bitmap outputs, all in device memory. The headline metric is arc-scans/s (slots examined by discharge
+passes and BFS expansions per second of solve time); solve ms is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one replica per GPU (the path does not shard; each rank solves its own copy).
+--impl reference times the CPU oracle (sequential FIFO push-relabel) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid3d_256x256x128: 6-connected, capacity U[1,1000] per direction, s->face z=0 and face z=127->t at 1e6"
+METRIC = "arc-scans/s"
+
+# Algorithmic bytes (what the method must move), per unit:
+B_SCAN_DIS = 12     # discharge arc scan: head 4 + residual 4 + d(w) 4 (+ the active bit)
+B_PUSH = 28         # push: rev 4 + two residual writes 8 + int64 atomic read-modify-write 16
+B_VISIT_DIS = 48    # active-vertex visit: row offsets 8 + d 4 + e 8 + d' 4 + addedExcess 16 + list 8
+B_SCAN_BFS = 12     # BFS arc scan: head 4 + reverse residual 4 + d(w) 4
+B_VISIT_BFS = 16    # BFS frontier vertex: row offsets 8 + list 8
+B_SLOT_FIXED = 20   # per solve and slot: residual reset (cap 4 + write 4) + flow output (cap 4 + res 4 + out 4)
+B_VERTEX_FIXED = 28  # per solve and vertex: state reset (d 4 + e 8 + addedExcess 8 + stamps 4) + cut 4
+B_VERTEX_GR = 12    # per global relabel and vertex: label reset 4 + rebuild (label 4 + excess ... 4)
+
+
+def model_bytes(st: dict, n: int, m: int) -> int:
+    return int(B_SCAN_DIS * st["scans_discharge"] + B_PUSH * st["pushes"] + B_VISIT_DIS * st["visits_discharge"]
+               + B_SCAN_BFS * st["scans_bfs"] + B_VISIT_BFS * st["visits_bfs"] + B_SLOT_FIXED * m
+               + B_VERTEX_FIXED * n + B_VERTEX_GR * n * st["global_relabels"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload():
+    from paper_1507_01926_gb300 import inputs, mf
+
+    g = inputs.config1()
+    csr = mf.build_csr(g.n, g.tail, g.head, g.cap)
+    return g, csr
+
+
+def golden_value():
+    p = os.path.join(ROOT, "tests", "golden", "config1.json")
+    if os.path.exists(p):
+        return json.load(open(p))["value"]
+    return None
+
+
+def cpu_baseline(g, seconds: float = 12.0):
+    """The oracle, as it stands, on a bounded sample: phase 1 on the full workload, stopped after a fixed
+    number of arc scans sized to about `seconds` of single-core work. Reports arc-scans/s."""
+    import oracle
+
+    probe = 20_000_000
+    r = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False, work_limit=probe)
+    rate = r["stats"]["scans"] / max(r["seconds"], 1e-9)
+    limit = int(max(probe, rate * seconds))
+    r = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False, work_limit=limit)
+    done = r["stats"]["scans"]
+    return {"value": done / r["seconds"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"sequential FIFO push-relabel phase 1 on the full {g.name}, stopped after {done} arc scans "
+                      f"({r['seconds']:.1f} s, {'complete' if not r['truncated'] else 'truncated'})",
+            "seconds": r["seconds"], "scans": done}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_1507_01926_gb300 import inputs
+
+    import oracle
+
+    g = inputs.config1()
+    per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    probe = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False,
+                           work_limit=10_000_000)
+    rate = probe["stats"]["scans"] / max(probe["seconds"], 1e-9)
+    limit = int(rate * per_step)
+    for _ in range(args.warmup):
+        oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False, work_limit=limit)
+    scans, secs = 0, 0.0
+    for _ in range(args.steps):
+        r = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False, work_limit=limit)
+        scans += r["stats"]["scans"]
+        secs += r["seconds"]
+    value = scans / secs
+    sample = (f"each step: sequential FIFO push-relabel phase 1 on the full {g.name}, stopped after about {limit} "
+              f"arc scans ({secs / max(args.steps, 1):.1f} s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "arcs": g.m},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1507_01926_gb300 import mf
+
+    g, csr = load_workload()
+    opt = mf.default_options(device=torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    row = torch.from_numpy(csr.row_offsets).to(dev)
+    head = torch.from_numpy(csr.head).to(dev)
+    cap = torch.from_numpy(csr.cap).to(dev)
+    rev = torch.from_numpy(csr.rev).to(dev)
+    torch.cuda.synchronize()
+    G = mf.Graph.from_device(g.n, row, head, cap, rev, g.s, g.t, opt, stream=stream)
+    del row, head, cap, rev
+    val = torch.zeros(1, dtype=torch.int64, device=dev)
+    flow = torch.zeros(csr.m, dtype=torch.int32, device=dev)
+    cutw = torch.zeros((g.n + 31) // 32, dtype=torch.int32, device=dev)
+
+    def step():
+        G.solve_device(val, flow, cutw, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    stream.synchronize()
+    warm_stats = G.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    per_step, stats = [], []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            stats.append(G.stats())
+        stream.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per_step)
+    scans = sum(s["scans_discharge"] + s["scans_bfs"] for s in stats)
+    if world > 1:
+        t = torch.tensor([total_ms, float(scans)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        total_ms_max, scans_all = float(mx[0]), float(sm[1])
+    else:
+        total_ms_max, scans_all = total_ms, float(scans)
+    value = scans_all / (total_ms_max / 1000.0)
+    flow_value = int(val.item())
+    gold = golden_value()
+
+    # roofline of the (only) kernel: the persistent solve kernel, one launch per step
+    peak, peak_kind = peaks()
+    mb = [model_bytes(s, g.n, csr.m) for s in stats]
+    achieved = (sum(mb) / len(mb)) / (statistics.mean(per_step) / 1000.0) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "solve_kernel_grid3d_256x256x128.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get("dram_bytes_per_launch")
+
+    if rank != 0:
+        G.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # end to end through the C-ABI with host buffers: create (H2D) + solve + outputs (D2H) + destroy
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+    h_row, h_head, h_cap, h_rev = pin(csr.row_offsets), pin(csr.head), pin(csr.cap), pin(csr.rev)
+    h_flow = torch.zeros(csr.m, dtype=torch.int32).pin_memory().numpy()
+    h_cut = torch.zeros((g.n + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    e2e_t, e2e_scans = [], 0
+    import ctypes
+
+    L = mf.lib()
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = ctypes.c_void_p()
+        mf._check(L.mf_create_graph(g.n, csr.m, mf._ptr(h_row), mf._ptr(h_head), mf._ptr(h_cap), mf._ptr(h_rev),
+                                    g.s, g.t, ctypes.byref(opt), ctypes.byref(h)))
+        v = ctypes.c_int64()
+        mf._check(L.mf_solve(h, ctypes.byref(v), mf._ptr(h_flow), mf._ptr(h_cut)))
+        s = mf.Stats()
+        L.mf_get_stats(h, ctypes.byref(s))
+        L.mf_destroy_graph(h)
+        dt = time.perf_counter() - t0
+        assert v.value == flow_value
+        if i > 0:  # first call warms the allocator and the pinned path
+            e2e_t.append(dt)
+            e2e_scans += s.scans_discharge + s.scans_bfs
+    h2d = 8 * (g.n + 1) + 4 * csr.m + 4 * csr.m + 8 * csr.m
+    d2h = 8 + 4 * csr.m + 4 * ((g.n + 31) // 32)
+    e2e = {"value": e2e_scans / sum(e2e_t), "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": 1000 * statistics.mean(e2e_t),
+           "includes": "mf_create_graph (H2D from pinned memory + on-device validation) + mf_solve (flow, cut D2H)"}
+
+    cpu = None if args.no_cpu_baseline else cpu_baseline(g)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "slots": csr.m, "arcs": g.m, "global_batch": world,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (about 1.3 GB of device state per solve)"},
+        "solve_ms": statistics.median(per_step), "solve_ms_all": [round(x, 3) for x in per_step],
+        "preflow_ms": statistics.median(s["preflow_ms"] for s in stats),
+        "flow_value": flow_value, "flow_value_matches_oracle": (gold == flow_value) if gold is not None else None,
+        "rounds": stats[-1]["rounds"], "global_relabels": stats[-1]["global_relabels"],
+        "scans_per_solve": scans / args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "mf::solve_kernel",
+                     "model_bytes_per_launch": statistics.mean(mb)},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
+        "grid": [warm_stats["grid_blocks"], warm_stats["block_threads"]],
+    }
+    print(json.dumps(line), flush=True)
+    G.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

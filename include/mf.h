@@ -1,0 +1,202 @@
+/*
+ * libmf — maximum flow / minimum cut on one GB300 GPU (sm_103a) by the
+ * synchronous parallel push-relabel algorithm of Baumstark, Blelloch and Shun,
+ * "Efficient Implementation of a Synchronous Parallel Push-Relabel Algorithm"
+ * (arXiv:1507.01926), Section 3, Section 3.1, Algorithms 1 and 2.
+ *
+ * Problem (Section 2): a directed graph with integer capacities c >= 0, a
+ * source s and a sink t; find a maximum flow f, its value |f|, and the minimal
+ * source side S_min of a minimum cut (the vertices reachable from s in the
+ * residual graph G_f of any maximum flow; unique).
+ *
+ * Graph format ("paired slots", the inline-reverse adjacency arrays of Section
+ * 4.2): a CSR over n vertices whose m entries ("slots") are directed arcs.
+ * Slot a lies in the row of its tail, head[a] is its head, cap[a] >= 0 its
+ * capacity, and rev[a] is the slot of the opposite direction (head[a] ->
+ * tail(a)), so that rev[rev[a]] == a and rev[a] != a. An input arc (u,v,c)
+ * with no partner is stored as the pair (u->v, c) / (v->u, 0); antiparallel
+ * input arcs (u,v,c1), (v,u,c2) may share one pair (c1 / c2). Residual
+ * capacities of a pair always sum to cap[a] + cap[rev[a]], which must not
+ * exceed INT32_MAX. mf_build_csr produces this format from an arc list.
+ *
+ * Arithmetic is exact integer: int32 residual capacities, int64 excesses and
+ * flow value. Per-slot flow is f(a) = max(0, cap[a] - residual[a]).
+ *
+ * Ownership: every input array belongs to the caller and is only read during
+ * the call (the library copies what it needs). Output arrays are allocated by
+ * the caller, except those of mf_build_csr (freed with mf_free_csr).
+ *
+ * Errors: every int-returning call returns MF_OK (0), MF_PENDING (1, only
+ * mf_poll) or a negative MF_ERR_* code; mf_last_error() then describes the
+ * last failure of the calling thread. Calls on one mf_graph must not overlap;
+ * different graphs may be used from different threads.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MF_OK 0
+#define MF_PENDING 1
+#define MF_ERR_INVALID_ARG (-1)  /* bad size, index out of range, null pointer, negative capacity */
+#define MF_ERR_BAD_PAIRING (-2)  /* rev[rev[a]] != a, rev[a] == a, or head[rev[a]] != tail(a) */
+#define MF_ERR_S_EQ_T (-3)       /* source equals sink */
+#define MF_ERR_CAP_OVERFLOW (-4) /* cap[a] + cap[rev[a]] > INT32_MAX */
+#define MF_ERR_OOM (-5)          /* device or host allocation failed */
+#define MF_ERR_OVER_BUDGET (-6)  /* instance larger than the service's device-memory budget */
+#define MF_ERR_ITER_LIMIT (-7)   /* round limit (mf_options.max_rounds) reached */
+#define MF_ERR_TIMEOUT (-8)      /* a device-side wait exceeded mf_options.timeout_ms */
+#define MF_ERR_CUDA (-9)         /* a CUDA runtime call failed */
+#define MF_ERR_INTERNAL (-10)    /* a self-check of the solver failed */
+#define MF_ERR_TOO_LARGE (-11)   /* n or m beyond the int32 limits of the device layout */
+#define MF_ERR_UNKNOWN_TICKET (-12)
+
+/* Tuning and safety limits. Fill with mf_default_options, then override. */
+typedef struct mf_options {
+  /* Global relabeling runs when gr_freq * work > gr_alpha * n + m, work being
+   * the sum of (out-degree + work_beta) over relabels since the last one
+   * (Algorithm 1; defaults 0.5, 6, 12 from the paper). */
+  double gr_freq;
+  int32_t gr_alpha;
+  int32_t work_beta;
+  /* Degree bins of the discharge and BFS kernels: a vertex of degree
+   * <= bin_thread is handled by one thread, <= bin_warp by one warp, larger
+   * by a whole CTA. */
+  int32_t bin_thread;
+  int32_t bin_warp;
+  /* Persistent-kernel shape: threads per CTA (multiple of 32, 64..512) and
+   * CTAs per SM (0 = as many as fit). */
+  int32_t block_threads;
+  int32_t blocks_per_sm;
+  /* Safety limits: maximum push-relabel rounds per phase (0 = 2,000,000)
+   * and the longest device-side wait before MF_ERR_TIMEOUT. */
+  int64_t max_rounds;
+  int32_t timeout_ms;
+  /* 1: stop after the maximum preflow (no per-arc flow; the cut is the set
+   * reachable from s and from every vertex holding excess, which equals
+   * S_min). */
+  int32_t cut_only;
+  /* CUDA device ordinal the graph lives on. */
+  int32_t device;
+} mf_options;
+
+/* Counters of the last solve. Arc scans count every slot examined by a
+ * discharge pass or a BFS expansion. */
+typedef struct mf_stats {
+  int64_t rounds;           /* push-relabel rounds, both phases */
+  int64_t rounds_phase1;
+  int64_t global_relabels;  /* BFS relabels, both phases */
+  int64_t bfs_levels;       /* BFS levels over all BFS runs */
+  int64_t scans_discharge;
+  int64_t scans_bfs;
+  int64_t pushes;
+  int64_t relabels;
+  int64_t visits_discharge; /* working-set entries discharged */
+  int64_t visits_bfs;       /* frontier entries expanded */
+  double solve_ms;          /* device time of the whole solve (CUDA events) */
+  double preflow_ms;        /* device time to the maximum preflow */
+  int32_t grid_blocks;      /* persistent-kernel CTAs */
+  int32_t block_threads;
+} mf_stats;
+
+typedef struct mf_graph mf_graph;
+typedef struct mf_batch mf_batch;
+typedef struct mf_service mf_service;
+typedef int64_t mf_ticket;
+
+/* Paired-slot CSR produced by mf_build_csr (arrays malloc'd by the library). */
+typedef struct mf_csr {
+  int32_t n;
+  int64_t m;            /* slots */
+  int64_t *row_offsets; /* n + 1 */
+  int32_t *head;        /* m */
+  int32_t *cap;         /* m */
+  int64_t *rev;         /* m */
+  int64_t *arc_slot;    /* m_in: slot holding input arc i, -1 for a dropped self-loop */
+  int64_t dropped_self_loops;
+} mf_csr;
+
+/* Host description of one instance (arrays in host memory). */
+typedef struct mf_graph_desc {
+  int32_t n;
+  int64_t m;
+  const int64_t *row_offsets;
+  const int32_t *head;
+  const int32_t *cap;
+  const int64_t *rev;
+  int32_t s, t;
+} mf_graph_desc;
+
+void mf_default_options(mf_options *opt);
+
+/* Last error message of the calling thread ("" if none). */
+const char *mf_last_error(void);
+
+/*
+ * Builds the paired-slot CSR from an input arc list (tail[i] -> head[i],
+ * capacity cap[i] >= 0, 0 <= m_in). Self-loops are dropped (counted in
+ * dropped_self_loops, arc_slot = -1). For every unordered vertex pair the k-th
+ * input arc u->v is paired with the k-th input arc v->u (input order); unpaired
+ * arcs get a reverse slot of capacity 0. Rows are sorted by head, ties in
+ * input order. Returns MF_ERR_CAP_OVERFLOW if a pair's capacities sum beyond
+ * INT32_MAX, MF_ERR_TOO_LARGE if the slots exceed INT32_MAX.
+ */
+int mf_build_csr(int32_t n, int64_t m_in, const int32_t *tail, const int32_t *head, const int32_t *cap,
+                 mf_csr *out);
+void mf_free_csr(mf_csr *csr);
+
+/*
+ * Copies a paired-slot CSR (host arrays, format above) to the device of
+ * opt->device and validates it there. n >= 2, 0 <= m < 2^31, 0 <= s, t < n,
+ * s != t. opt may be NULL (defaults). On success *out owns device memory
+ * until mf_destroy_graph.
+ */
+int mf_create_graph(int32_t n, int64_t m, const int64_t *row_offsets, const int32_t *head, const int32_t *cap,
+                    const int64_t *rev, int32_t s, int32_t t, const mf_options *opt, mf_graph **out);
+
+/* Same, from arrays already in device memory of opt->device, read on `stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+int mf_create_graph_device(int32_t n, int64_t m, const int64_t *d_row_offsets, const int32_t *d_head,
+                           const int32_t *d_cap, const int64_t *d_rev, int32_t s, int32_t t, const mf_options *opt,
+                           void *stream, mf_graph **out);
+
+/*
+ * Solves max flow on g (Algorithms 1 and 2 for the maximum preflow, then the
+ * preflow becomes a flow by returning excess to s; Section 2.1). Outputs in
+ * host memory, each nullable: *flow_value = |f|; arc_flow[a] (m entries) =
+ * flow on slot a; cut_bits (ceil(n/32) words) has bit v%32 of word v/32 set
+ * iff v is in S_min. With opt.cut_only, arc_flow must be NULL.
+ * May be called repeatedly; each call starts from the input capacities.
+ */
+int mf_solve(mf_graph *g, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_bits);
+
+/* Same with outputs in device memory, enqueued on `stream` (cudaStream_t);
+ * returns after the solve finished (it reads the status word back). */
+int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d_arc_flow, uint32_t *d_cut_bits);
+
+/* Counters of the last solve on g. */
+int mf_get_stats(const mf_graph *g, mf_stats *out);
+
+/*
+ * Inspection for tests: initialises phase 1 (Algorithm 1 initialisation),
+ * runs the global relabel and then at most `rounds` push-relabel rounds of
+ * phase 1; when final_relabel != 0 runs one more global relabel after them.
+ * Copies the state out (host arrays, each nullable): residual[m] per slot,
+ * label[n] (the source's label reads n, the sink's 0), excess[n]. Returns MF_OK
+ * or MF_PENDING-free error codes; *rounds_done (nullable) = rounds run.
+ */
+int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *residual, int32_t *label,
+                  int64_t *excess, int64_t *rounds_done);
+
+void mf_destroy_graph(mf_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

@@ -1,0 +1,540 @@
+// Host side of the C-ABI (include/mf.h): graph objects, validation on the
+// device, launch of the persistent solver, error reporting.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "mf.h"
+#include "mf_device.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+const char *last_error() { return g_err.c_str(); }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(MF_ERR_OOM, "%s: out of device memory", what);
+  }
+  return fail(MF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ validation
+
+enum : unsigned {
+  V_ROW = 1u,        // row offsets not monotone / wrong ends
+  V_HEAD = 2u,       // head out of range
+  V_REV = 4u,        // rev out of range or rev[a] == a
+  V_CAP = 8u,        // negative capacity
+  V_PAIR = 16u,      // rev[rev[a]] != a
+  V_TAIL = 32u,      // head[rev[a]] != tail(a)
+  V_OVERFLOW = 64u,  // cap[a] + cap[rev[a]] > INT32_MAX
+};
+
+__global__ void k_check_rows(int n, long long m, const long long *row64, int *row32, unsigned *flags) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= n; v += (long long)gridDim.x * blockDim.x) {
+    const long long x = row64[v];
+    bool bad = x < 0 || x > m;
+    if (v == 0 && x != 0) bad = true;
+    if (v == n && x != m) bad = true;
+    if (v < n && x > row64[v + 1]) bad = true;
+    if (bad) atomicOr(flags, V_ROW);
+    row32[v] = (int)(bad ? 0 : x);
+  }
+}
+
+__global__ void k_check_slots(int n, long long m, const int *head, const int *cap, const long long *rev64,
+                              int *rev32, unsigned *flags) {
+  unsigned f = 0;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m; a += (long long)gridDim.x * blockDim.x) {
+    const int h = head[a];
+    if (h < 0 || h >= n) f |= V_HEAD;
+    if (cap[a] < 0) f |= V_CAP;
+    const long long r = rev64[a];
+    if (r < 0 || r >= m || r == a) {
+      f |= V_REV;
+      rev32[a] = (int)a;
+    } else {
+      rev32[a] = (int)r;
+    }
+  }
+  if (f) atomicOr(flags, f);
+}
+
+__global__ void k_check_pairs(int n, long long m, const int *row, const int *head, const int *cap, const int *rev,
+                              unsigned *flags, unsigned long long *m_arcs) {
+  unsigned f = 0;
+  unsigned long long cnt = 0;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m; a += (long long)gridDim.x * blockDim.x) {
+    // tail(a): last v with row[v] <= a
+    int lo = 0, hi = n;  // row[lo] <= a < row[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (row[mid] <= a) lo = mid; else hi = mid;
+    }
+    const int ra = rev[a];
+    if (rev[ra] != (int)a) f |= V_PAIR;
+    if (head[ra] != lo) f |= V_TAIL;
+    if ((long long)cap[a] + (long long)cap[ra] > 2147483647LL) f |= V_OVERFLOW;
+    if (cap[a] > 0) cnt++;
+  }
+  if (f) atomicOr(flags, f);
+  if (cnt) atomicAdd(m_arcs, cnt);
+}
+
+static int flags_to_status(unsigned f) {
+  if (f & (V_ROW | V_HEAD | V_REV | V_CAP)) {
+    return fail(MF_ERR_INVALID_ARG, "invalid graph:%s%s%s%s", (f & V_ROW) ? " row_offsets not a valid CSR;" : "",
+                (f & V_HEAD) ? " head out of range;" : "", (f & V_REV) ? " rev out of range or rev[a]==a;" : "",
+                (f & V_CAP) ? " negative capacity;" : "");
+  }
+  if (f & (V_PAIR | V_TAIL))
+    return fail(MF_ERR_BAD_PAIRING, "bad reverse pairing:%s%s", (f & V_PAIR) ? " rev[rev[a]] != a;" : "",
+                (f & V_TAIL) ? " head[rev[a]] != tail(a);" : "");
+  if (f & V_OVERFLOW) return fail(MF_ERR_CAP_OVERFLOW, "cap[a] + cap[rev[a]] exceeds INT32_MAX");
+  return MF_OK;
+}
+
+// ------------------------------------------------------------------ graph
+
+static void free_graph_buffers(mf_graph *g) {
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vl, g->dn, g->e, g->added, g->disc,
+                g->list[0], g->list[1], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  if (g->h_ctl) cudaFreeHost(g->h_ctl);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+}
+
+static int dalloc(void **p, size_t bytes, const char *what) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return MF_OK;
+}
+
+#define TRY(x)               \
+  do {                       \
+    int _rc = (x);           \
+    if (_rc != MF_OK) {      \
+      mf_destroy_graph(g);   \
+      return _rc;            \
+    }                        \
+  } while (0)
+
+#define TRYC(x, what)                       \
+  do {                                      \
+    cudaError_t _e = (x);                   \
+    if (_e != cudaSuccess) {                \
+      int _rc = cuda_fail(_e, what);        \
+      mf_destroy_graph(g);                  \
+      return _rc;                           \
+    }                                       \
+  } while (0)
+
+int alloc_state(mf_graph *g) {
+  const size_t n = (size_t)g->n, m = (size_t)g->m;
+  int rc;
+  if ((rc = dalloc((void **)&g->row, (n + 1) * 4, "cudaMalloc row"))) return rc;
+  if ((rc = dalloc((void **)&g->head, m * 4, "cudaMalloc head"))) return rc;
+  if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
+  if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
+  if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
+  if ((rc = dalloc((void **)&g->vl, n * 8, "cudaMalloc labels"))) return rc;
+  if ((rc = dalloc((void **)&g->dn, n * 4, "cudaMalloc d'"))) return rc;
+  if ((rc = dalloc((void **)&g->e, n * 8, "cudaMalloc excess"))) return rc;
+  if ((rc = dalloc((void **)&g->added, n * 8, "cudaMalloc addedExcess"))) return rc;
+  if ((rc = dalloc((void **)&g->disc, n * 4, "cudaMalloc discovery stamps"))) return rc;
+  if ((rc = dalloc((void **)&g->list[0], n * 4, "cudaMalloc list"))) return rc;
+  if ((rc = dalloc((void **)&g->list[1], n * 4, "cudaMalloc list"))) return rc;
+  if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
+  if ((rc = dalloc((void **)&g->snk, (size_t)g->ninst * 4, "cudaMalloc sinks"))) return rc;
+  if ((rc = dalloc((void **)&g->ctl, sizeof(Ctl), "cudaMalloc control block"))) return rc;
+  if ((rc = dalloc((void **)&g->d_value, (size_t)g->ninst * 8, "cudaMalloc value"))) return rc;
+  cudaError_t e = cudaMallocHost((void **)&g->h_ctl, sizeof(Ctl));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+  if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&g->ev1)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  return MF_OK;
+}
+
+// Validates the copied CSR (row64/rev64 in device memory) and fills the
+// int32 device arrays; computes m_arcs.
+int validate_on_device(mf_graph *g, const long long *row64, const long long *rev64, cudaStream_t st) {
+  unsigned *flags = nullptr;
+  unsigned long long *marcs = nullptr;
+  cudaError_t e = cudaMalloc((void **)&flags, 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc flags");
+  marcs = reinterpret_cast<unsigned long long *>(flags) + 1;
+  cudaMemsetAsync(flags, 0, 16, st);
+  const int T = 256;
+  const int Gn = (int)((g->n + 1 + T - 1) / T < 65535 * 16 ? (g->n + 1 + T - 1) / T : 65535 * 16);
+  const long long gm = (g->m + T - 1) / T;
+  const int Gm = (int)(gm < 1 ? 1 : (gm < 65535LL * 16 ? gm : 65535LL * 16));
+  k_check_rows<<<Gn, T, 0, st>>>(g->n, g->m, row64, g->row, flags);
+  k_check_slots<<<Gm, T, 0, st>>>(g->n, g->m, g->head, g->cap, rev64, g->rev, flags);
+  unsigned h[4] = {0, 0, 0, 0};
+  e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(flags);
+    return cuda_fail(e, "graph validation");
+  }
+  if (h[0] == 0 && g->m > 0) {
+    k_check_pairs<<<Gm, T, 0, st>>>(g->n, g->m, g->row, g->head, g->cap, g->rev, flags, marcs);
+    e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(flags);
+      return cuda_fail(e, "graph validation");
+    }
+  }
+  cudaFree(flags);
+  g->m_arcs = (long long)((unsigned long long)h[2] | ((unsigned long long)h[3] << 32));
+  return flags_to_status(h[0]);
+}
+
+int launch_config(mf_graph *g) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (!prop.cooperativeLaunch) return fail(MF_ERR_CUDA, "device %d lacks cooperative launch", g->device);
+  int bps = 0;
+  if (solver_occupancy(g->opt.block_threads, &bps) || bps < 1)
+    return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", g->opt.block_threads);
+  if (g->opt.blocks_per_sm > 0 && g->opt.blocks_per_sm < bps) bps = g->opt.blocks_per_sm;
+  g->grid = bps * prop.multiProcessorCount;
+  g->block = g->opt.block_threads;
+  return MF_OK;
+}
+
+int check_options(const mf_options *o) {
+  if (o->block_threads < 64 || o->block_threads > 512 || o->block_threads % 32)
+    return fail(MF_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [64, 512]");
+  if (o->bin_thread < 0 || o->bin_thread > 8) return fail(MF_ERR_INVALID_ARG, "bin_thread must be in [0, 8]");
+  if (o->bin_warp < o->bin_thread) return fail(MF_ERR_INVALID_ARG, "bin_warp must be >= bin_thread");
+  if (!(o->gr_freq > 0)) return fail(MF_ERR_INVALID_ARG, "gr_freq must be > 0");
+  if (o->gr_alpha < 0 || o->work_beta < 0) return fail(MF_ERR_INVALID_ARG, "gr_alpha, work_beta must be >= 0");
+  if (o->timeout_ms <= 0) return fail(MF_ERR_INVALID_ARG, "timeout_ms must be > 0");
+  if (o->max_rounds < 0) return fail(MF_ERR_INVALID_ARG, "max_rounds must be >= 0");
+  return MF_OK;
+}
+
+Dev make_dev(const mf_graph *g) {
+  Dev D;
+  memset(&D, 0, sizeof(D));
+  D.n = g->n;
+  D.m = (int)g->m;
+  D.n_cap = g->n_cap;
+  D.ncap = g->ncap;
+  D.row = g->row;
+  D.head = g->head;
+  D.rev = g->rev;
+  D.cap = g->cap;
+  D.rr = g->rr;
+  D.vl = g->vl;
+  D.dn = g->dn;
+  D.e = g->e;
+  D.added = g->added;
+  D.disc = g->disc;
+  D.list[0] = g->list[0];
+  D.list[1] = g->list[1];
+  D.src = g->src;
+  D.snk = g->snk;
+  D.ninst = g->ninst;
+  D.ctl = g->ctl;
+  D.bin_thread = g->opt.bin_thread;
+  D.bin_warp = g->opt.bin_warp;
+  D.beta = g->opt.work_beta;
+  const double thr = ((double)g->opt.gr_alpha * (double)g->n_total_for_gr + (double)g->m_arcs) / g->opt.gr_freq;
+  D.gr_threshold = thr > 9.0e18 ? (long long)9e18 : (long long)thr;
+  D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
+  D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
+  D.mode = MODE_SOLVE;
+  D.cut_only = g->opt.cut_only;
+  return D;
+}
+
+// Runs the persistent kernel once with D; fills g->h_ctl and g->stats.
+int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  cudaEventRecord(g->ev0, st);
+  e = launch_solver(D, g->grid, g->block, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the solver");
+  cudaEventRecord(g->ev1, st);
+  e = cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solver");
+  const Ctl &c = *g->h_ctl;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+  mf_stats &s = g->stats;
+  s.rounds = c.rounds;
+  s.rounds_phase1 = c.rounds_phase1;
+  s.global_relabels = c.grs;
+  s.bfs_levels = c.levels;
+  s.scans_discharge = c.scans_dis;
+  s.scans_bfs = c.scans_bfs;
+  s.pushes = c.pushes;
+  s.relabels = c.relabels;
+  s.visits_discharge = c.visits_dis;
+  s.visits_bfs = c.visits_bfs;
+  s.solve_ms = ms;
+  s.preflow_ms = c.t_preflow > c.t_start ? (double)(c.t_preflow - c.t_start) * 1e-6 : 0.0;
+  s.grid_blocks = g->grid;
+  s.block_threads = g->block;
+  if (c.err) {
+    static const char *where[] = {"init barrier", "saturation barrier", "relabel BFS", "working-set rebuild",
+                                  "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
+                                  "phase-2 excess check", "cut BFS", "round limit", "list capacity"};
+    const char *w = (c.err_where >= 0 && c.err_where <= 11) ? where[c.err_where] : "?";
+    if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
+    if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);
+    if (c.err == MF_ERR_INTERNAL && c.err_where == 8)
+      return fail(MF_ERR_INTERNAL, "self-check failed: %lld vertices kept excess", c.leftover);
+    if (c.err == MF_ERR_INTERNAL) return fail(MF_ERR_INTERNAL, "self-check failed (%s)", w);
+    return fail(c.err, "device error %d (%s)", c.err, w);
+  }
+  return MF_OK;
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+extern "C" {
+
+void mf_default_options(mf_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->gr_freq = 0.5;
+  o->gr_alpha = 6;
+  o->work_beta = 12;
+  o->bin_thread = 8;
+  o->bin_warp = 1024;
+  o->block_threads = 256;
+  o->blocks_per_sm = 0;
+  o->max_rounds = 0;
+  o->timeout_ms = 5000;
+  o->cut_only = 0;
+  o->device = 0;
+}
+
+const char *mf_last_error(void) { return last_error(); }
+
+static int create_common(int32_t n, int64_t m, int32_t s, int32_t t, const mf_options *opt, mf_graph **out,
+                         mf_graph **gp) {
+  clear_error();
+  if (!out) return fail(MF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 2) return fail(MF_ERR_INVALID_ARG, "n must be >= 2");
+  if (n > UNV - 4) return fail(MF_ERR_TOO_LARGE, "n exceeds the label range (%d)", UNV - 4);
+  if (m < 0) return fail(MF_ERR_INVALID_ARG, "m must be >= 0");
+  if (m > 2147483647LL - 1) return fail(MF_ERR_TOO_LARGE, "m exceeds INT32_MAX slots");
+  if (s < 0 || s >= n || t < 0 || t >= n) return fail(MF_ERR_INVALID_ARG, "s or t out of range");
+  if (s == t) return fail(MF_ERR_S_EQ_T, "source equals sink");
+  mf_options o;
+  if (opt)
+    o = *opt;
+  else
+    mf_default_options(&o);
+  int rc = check_options(&o);
+  if (rc) return rc;
+  cudaError_t e = cudaSetDevice(o.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  mf_graph *g = new mf_graph();
+  g->opt = o;
+  g->device = o.device;
+  g->n = n;
+  g->m = m;
+  g->s = s;
+  g->t = t;
+  g->ninst = 1;
+  g->n_cap = n;
+  g->n_total_for_gr = n;
+  *gp = g;
+  return MF_OK;
+}
+
+int mf_create_graph(int32_t n, int64_t m, const int64_t *row_offsets, const int32_t *head, const int32_t *cap,
+                    const int64_t *rev, int32_t s, int32_t t, const mf_options *opt, mf_graph **out) {
+  mf_graph *g = nullptr;
+  int rc = create_common(n, m, s, t, opt, out, &g);
+  if (rc) return rc;
+  if (!row_offsets || (m > 0 && (!head || !cap || !rev))) {
+    delete g;
+    return fail(MF_ERR_INVALID_ARG, "NULL array");
+  }
+  TRYC(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  g->own_stream = true;
+  TRY(alloc_state(g));
+  long long *row64 = nullptr, *rev64 = nullptr;
+  TRYC(cudaMalloc((void **)&row64, ((size_t)n + 1) * 8), "cudaMalloc staging");
+  cudaError_t e = cudaMalloc((void **)&rev64, (size_t)(m > 0 ? m : 1) * 8);
+  if (e != cudaSuccess) {
+    cudaFree(row64);
+    TRYC(e, "cudaMalloc staging");
+  }
+  e = cudaMemcpyAsync(row64, row_offsets, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(rev64, rev, (size_t)m * 8, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->head, head, (size_t)m * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->cap, cap, (size_t)m * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->src, &g->s, 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->snk, &g->t, 4, cudaMemcpyHostToDevice, g->stream);
+  if (e != cudaSuccess) {
+    cudaFree(row64);
+    cudaFree(rev64);
+    TRYC(e, "host-to-device copy");
+  }
+  rc = validate_on_device(g, row64, rev64, g->stream);
+  cudaFree(row64);
+  cudaFree(rev64);
+  TRY(rc);
+  TRY(launch_config(g));
+  *out = g;
+  return MF_OK;
+}
+
+int mf_create_graph_device(int32_t n, int64_t m, const int64_t *d_row_offsets, const int32_t *d_head,
+                           const int32_t *d_cap, const int64_t *d_rev, int32_t s, int32_t t, const mf_options *opt,
+                           void *stream, mf_graph **out) {
+  mf_graph *g = nullptr;
+  int rc = create_common(n, m, s, t, opt, out, &g);
+  if (rc) return rc;
+  if (!d_row_offsets || (m > 0 && (!d_head || !d_cap || !d_rev))) {
+    delete g;
+    return fail(MF_ERR_INVALID_ARG, "NULL array");
+  }
+  g->stream = (cudaStream_t)stream;
+  g->own_stream = false;
+  TRY(alloc_state(g));
+  cudaError_t e = cudaSuccess;
+  if (m > 0) e = cudaMemcpyAsync(g->head, d_head, (size_t)m * 4, cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->cap, d_cap, (size_t)m * 4, cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->src, &g->s, 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->snk, &g->t, 4, cudaMemcpyHostToDevice, g->stream);
+  TRYC(e, "device copy");
+  TRY(validate_on_device(g, (const long long *)d_row_offsets, (const long long *)d_rev, g->stream));
+  TRY(launch_config(g));
+  *out = g;
+  return MF_OK;
+}
+
+void mf_destroy_graph(mf_graph *g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  free_graph_buffers(g);
+  delete g;
+}
+
+static int solve_into(mf_graph *g, cudaStream_t st, int64_t *d_value, int32_t *d_flow, uint32_t *d_cut) {
+  if (g->opt.cut_only && d_flow) return fail(MF_ERR_INVALID_ARG, "cut_only solves produce no per-arc flow");
+  Dev D = make_dev(g);
+  D.out_value = d_value ? reinterpret_cast<long long *>(d_value) : g->d_value;
+  D.out_flow = d_flow;
+  D.out_cut = d_cut;
+  return run_kernel(g, D, st);
+}
+
+int mf_solve(mf_graph *g, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_bits) {
+  clear_error();
+  if (!g) return fail(MF_ERR_INVALID_ARG, "graph is NULL");
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (arc_flow && !g->d_flow) {
+    e = cudaMalloc((void **)&g->d_flow, (size_t)(g->m > 0 ? g->m : 1) * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc flow output");
+  }
+  const size_t words = ((size_t)g->n + 31) / 32;
+  if (cut_bits && !g->d_cut) {
+    e = cudaMalloc((void **)&g->d_cut, words * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc cut output");
+  }
+  int rc = solve_into(g, g->stream, nullptr, arc_flow ? g->d_flow : nullptr, cut_bits ? g->d_cut : nullptr);
+  if (rc) return rc;
+  if (flow_value) *flow_value = g->h_ctl->value;
+  if (arc_flow && g->m > 0) e = cudaMemcpyAsync(arc_flow, g->d_flow, (size_t)g->m * 4, cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess && cut_bits) e = cudaMemcpyAsync(cut_bits, g->d_cut, words * 4, cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of the outputs");
+  return MF_OK;
+}
+
+int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d_arc_flow, uint32_t *d_cut_bits) {
+  clear_error();
+  if (!g) return fail(MF_ERR_INVALID_ARG, "graph is NULL");
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return solve_into(g, (cudaStream_t)stream, d_flow_value, d_arc_flow, d_cut_bits);
+}
+
+int mf_get_stats(const mf_graph *g, mf_stats *out) {
+  clear_error();
+  if (!g || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  *out = g->stats;
+  return MF_OK;
+}
+
+int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *residual, int32_t *label,
+                  int64_t *excess, int64_t *rounds_done) {
+  clear_error();
+  if (!g) return fail(MF_ERR_INVALID_ARG, "graph is NULL");
+  if (rounds < 0) return fail(MF_ERR_INVALID_ARG, "rounds must be >= 0");
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  Dev D = make_dev(g);
+  D.mode = MODE_ROUNDS;
+  D.stop_rounds = rounds;
+  D.final_gr = final_relabel ? 1 : 0;
+  int rc = run_kernel(g, D, g->stream);
+  if (rc) return rc;
+  if (rounds_done) *rounds_done = g->h_ctl->stopped_round;
+  const size_t n = (size_t)g->n, m = (size_t)g->m;
+  if (residual && m > 0) {
+    int2 *tmp = (int2 *)malloc(m * sizeof(int2));
+    if (!tmp) return fail(MF_ERR_OOM, "host allocation");
+    e = cudaMemcpyAsync(tmp, g->rr, m * sizeof(int2), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    for (size_t a = 0; a < m && e == cudaSuccess; a++) residual[a] = tmp[a].x;
+    free(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy");
+  }
+  if (label) {
+    int2 *tmp = (int2 *)malloc(n * sizeof(int2));
+    if (!tmp) return fail(MF_ERR_OOM, "host allocation");
+    e = cudaMemcpyAsync(tmp, g->vl, n * sizeof(int2), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    for (size_t v = 0; v < n && e == cudaSuccess; v++) label[v] = tmp[v].x > g->n ? g->n : tmp[v].x;
+    free(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy");
+  }
+  if (excess) {
+    e = cudaMemcpyAsync(excess, g->e, n * 8, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy");
+  }
+  return MF_OK;
+}
+
+}  // extern "C"

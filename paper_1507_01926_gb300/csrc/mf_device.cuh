@@ -1,0 +1,75 @@
+// Device-side data model of the solver (shared by the kernels and the host
+// launch code). Everything is plain integer state resident in HBM.
+#pragma once
+#include <stdint.h>
+
+namespace mf {
+
+// Sentinel label of a vertex not yet reached by a BFS; a source-role vertex
+// carries UNV + 1 during a BFS so that it is never discovered.
+constexpr int UNV = 0x3fffffff;
+
+// What the persistent kernel does.
+enum Mode : int {
+  MODE_SOLVE = 0,   // phase 1, phase 2 (unless cut_only), cut, outputs
+  MODE_ROUNDS = 1,  // phase 1 for at most stop_rounds rounds (+ optional final BFS relabel), no outputs
+};
+
+// Control block in device memory, zeroed before every launch.
+struct Ctl {
+  unsigned bar_count;  // grid barrier arrivals
+  unsigned bar_gen;    // grid barrier generation
+  int err;             // 0 or an MF_ERR_* code
+  int err_where;       // which wait or check failed
+  int cnt[3];          // list sizes of generations g % 3
+  int live[3];         // live (non-dead) entries of generations g % 3
+  long long work[2];   // per-round relabel work, by round parity
+  long long value;     // flow value (excess of the sink after phase 1)
+  long long leftover;  // vertices still holding excess after phase 2
+  // statistics
+  long long rounds, rounds_phase1, grs, levels;
+  long long scans_dis, scans_bfs, pushes, relabels;
+  long long visits_dis, visits_bfs;
+  unsigned long long t_start, t_preflow, t_end;  // %globaltimer, ns
+  int stopped_round;   // MODE_ROUNDS: rounds run
+};
+
+// Device view of one (possibly multi-instance) graph.
+struct Dev {
+  int n;        // vertices (all instances)
+  int m;        // slots (all instances)
+  int n_cap;    // label cap when ncap == nullptr (single instance)
+  const int *__restrict__ ncap;  // per-vertex label cap (its instance's n), or nullptr
+  const int *__restrict__ row;   // n + 1 slot offsets
+  const int *__restrict__ head;  // m
+  const int *__restrict__ rev;   // m
+  const int *__restrict__ cap;   // m, input capacities (= initial residuals)
+  int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
+  int2 *vl;          // n: {label d, round stamp of active-set membership}
+  int *dn;           // n: d' (label after this round's discharge)
+  long long *e;      // n: excess
+  long long *added;  // n: excess received this round by a vertex being discharged
+  int *disc;         // n: round stamp of the last test-and-set discovery
+  int *list[2];      // vertex lists, generation g uses list[g & 1]
+  const int *src;    // sources (phase 1), one per instance
+  const int *snk;    // sinks (phase 1), one per instance
+  int ninst;
+  Ctl *ctl;
+  // options
+  int bin_thread;
+  int bin_warp;
+  int beta;
+  long long gr_threshold;  // global relabel when work since the last one exceeds this
+  long long max_rounds;
+  unsigned long long timeout_ns;
+  int mode;
+  long long stop_rounds;
+  int final_gr;
+  int cut_only;
+  // outputs (device pointers, each nullable)
+  long long *out_value;   // per instance
+  int *out_flow;          // m
+  unsigned *out_cut;      // ceil(n / 32)
+};
+
+}  // namespace mf

@@ -1,0 +1,51 @@
+// Internal declarations shared by the host-side translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mf.h"
+#include "mf_device.cuh"
+
+struct mf_graph {
+  int device = 0;
+  int n = 0;
+  long long m = 0;
+  int s = 0, t = 0;
+  int ninst = 1;
+  int n_cap = 0;               // label cap of a single instance (n)
+  long long n_total_for_gr = 0;  // n in the relabel threshold alpha * n + m
+  long long m_arcs = 0;        // slots with positive capacity
+  mf_options opt{};
+  mf_stats stats{};
+  int grid = 0, block = 0;
+  // device state
+  int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
+  int2 *rr = nullptr, *vl = nullptr;
+  int *dn = nullptr;
+  long long *e = nullptr, *added = nullptr;
+  int *disc = nullptr;
+  int *list[2] = {nullptr, nullptr};
+  int *src = nullptr, *snk = nullptr;
+  int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)
+  mf::Ctl *ctl = nullptr;
+  long long *d_value = nullptr;
+  int *d_flow = nullptr;
+  unsigned *d_cut = nullptr;
+  mf::Ctl *h_ctl = nullptr;    // pinned
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace mf {
+int fail(int code, const char *fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);
+int alloc_state(mf_graph *g);
+int validate_on_device(mf_graph *g, const long long *row64, const long long *rev64, cudaStream_t st);
+int launch_config(mf_graph *g);
+int check_options(const mf_options *o);
+Dev make_dev(const mf_graph *g);
+int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
+int solver_occupancy(int block_threads, int *blocks_per_sm);
+cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream);
+}  // namespace mf

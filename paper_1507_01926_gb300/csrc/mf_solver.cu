@@ -1,0 +1,898 @@
+// Synchronous parallel push-relabel (arXiv:1507.01926, Section 3.1 and
+// Algorithm 1) with parallel global relabeling (Section 3, Algorithm 2) as one
+// persistent cooperative kernel for sm_103a.
+//
+// One launch runs a whole solve: initialisation and source saturation,
+// phase 1 (rounds of discharge + apply, a BFS global relabel whenever the
+// relabel work since the last one exceeds the threshold), phase 2 (the same
+// rounds toward s return the excess that cannot reach t), the cut BFS from s
+// and the outputs. Phases are separated by a grid barrier whose waits are
+// bounded in time (MF_ERR_TIMEOUT instead of a hang).
+//
+// Data model (mf_device.cuh): CSR of paired slots with an inline copy of the
+// reverse residual (int2 rr[a] = {res[a], res[rev[a]]}, the "each edge also
+// stores the residual capacity of its reverse edge" layout of Section 4.2),
+// per-vertex int2 vl[v] = {label, round stamp of active-set membership},
+// int64 excess. Vertex lists are plain arrays filled by warp-aggregated
+// atomics; a list is consumed in tiles of blockDim entries that are binned in
+// shared memory by degree (thread / warp / CTA per vertex).
+//
+// Readings of the listing that the kernel follows (Algorithm 1):
+//  * the activity test of a neighbour w ("if e(w)") is membership of w in the
+//    current working set, kept as vl[w].y == round;
+//  * pushes use the local excess of the discharging vertex;
+//  * excess received by a vertex that is itself being discharged goes to its
+//    addedExcess (atomic), excess received by any other vertex is added to its
+//    excess directly (atomic; nobody reads it during the round);
+//  * the next working set holds every vertex that received excess (not the
+//    sink) plus every discharged vertex left with excess and d' < n, minus
+//    those whose label reached n; excess pushed into the sink accumulates into
+//    e(sink), which is the flow value;
+//  * arcs of one vertex are scanned in CSR order; a warp or CTA reproduces
+//    that order with an exclusive prefix sum of the pushable residuals;
+//  * the source keeps label n + 1 internally (equivalent to n: no label
+//    reaches n + 2, and relabels start from n);
+//  * after every global relabel the working set is rebuilt from all vertices
+//    with excess and 0 < d < n, and a phase ends only when a rebuild right
+//    after a global relabel finds no active vertex.
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <stdint.h>
+
+#include "mf.h"
+#include "mf_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mf {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int KT = 8;         // largest degree handled by one thread (register-cached arcs)
+constexpr int MAX_BLOCK = 512;  // largest CTA
+constexpr int MAX_WARPS = MAX_BLOCK / 32;
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ int *label_ptr(const Dev &D, int v) { return reinterpret_cast<int *>(&D.vl[v]); }
+__device__ __forceinline__ int *stamp_ptr(const Dev &D, int v) { return reinterpret_cast<int *>(&D.vl[v]) + 1; }
+
+__device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
+
+__device__ __forceinline__ void set_err(const Dev &D, int code, int where) {
+  if (atomicCAS(&D.ctl->err, 0, code) == 0) atomicExch(&D.ctl->err_where, where);
+}
+
+// Win rule of Section 3.1 for two active neighbours, on the labels at the
+// start of the round: v owns the pair iff d(v) = d(w) + 1, or d(v) < d(w) - 1,
+// or d(v) = d(w) and v < w. Exactly one of v, w wins.
+__device__ __forceinline__ bool wins(int dv, int dw, int v, int w) {
+  return (dv == dw + 1) || (dv < dw - 1) || (dv == dw && v < w);
+}
+
+// Push delta along slot a (reverse slot ra): res[a] -= delta, res[ra] += delta,
+// with the inline reverse copies updated alike. Each slot is one 64-bit word
+// {res, rres}; the win rule gives every pair a single pusher per round and the
+// pair sums stay within int32, so the packed adds never carry between halves.
+__device__ __forceinline__ void push_res(const Dev &D, int a, int ra, int delta) {
+  unsigned long long d64 = (unsigned long long)(unsigned)delta;
+  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[a]), (d64 << 32) - d64);
+  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[ra]), d64 - (d64 << 32));
+}
+
+// Appends one value per calling thread to list/cnt with one atomic per
+// converged group of lanes. Lists hold at most n entries (every list holds
+// distinct vertices); an overflow would be a solver bug and is reported as
+// MF_ERR_INTERNAL instead of being written.
+__device__ __forceinline__ void append(const Dev &D, int *list, int *cnt, int val) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(cnt, (int)g.size());
+  base = g.shfl(base, 0);
+  const int idx = base + (int)g.thread_rank();
+  if (idx < D.n)
+    list[idx] = val;
+  else
+    set_err(D, MF_ERR_INTERNAL, 11);
+}
+
+// Entries of list generation gen (never more than n).
+__device__ __forceinline__ int list_count(const Dev &D, int gen) { return min(__ldcg(&D.ctl->cnt[gen % 3]), D.n); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
+__device__ __forceinline__ int warp_min(int x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(FULL, x, o));
+  return x;
+}
+
+__device__ __forceinline__ long long warp_incl_scan(long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+struct Shared {
+  unsigned gen;
+  int pick;
+  int flag;
+  int imin[MAX_WARPS];
+  long long lsum[MAX_WARPS];
+  long long bval;
+};
+
+// Block-wide sum of a 64-bit value (all threads call; result valid in all).
+__device__ long long block_sum(long long x, Shared &sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  x = warp_sum(x);
+  __syncthreads();
+  if (lane == 0) sh.lsum[wid] = x;
+  __syncthreads();
+  long long t = 0;
+  for (int i = 0; i < nw; i++) t += sh.lsum[i];
+  __syncthreads();
+  return t;
+}
+
+// Grid barrier. Every wait is bounded by D.timeout_ns; on expiry the error
+// word is set and all blocks leave at their next barrier.
+__device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Ctl *c = D.ctl;
+    unsigned g = sh.gen;
+    __threadfence();
+    unsigned prev = atomicAdd(&c->bar_count, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      st_release(&c->bar_gen, g + 1);
+    } else {
+      unsigned long long t0 = gtimer();
+      unsigned spins = 0;
+      while (ld_acquire(&c->bar_gen) == g) {
+        if ((++spins & 31u) == 0 && gtimer() - t0 > D.timeout_ns) {
+          set_err(D, MF_ERR_TIMEOUT, where);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    sh.gen = g + 1;
+    __threadfence();
+  }
+  __syncthreads();
+  return vol_read(&D.ctl->err) == 0;
+}
+
+struct TStat {
+  long long scans_dis = 0, scans_bfs = 0, pushes = 0, relabels = 0, visits_dis = 0, visits_bfs = 0;
+};
+
+// ------------------------------------------------------------------ discharge
+//
+// Algorithm 1, inner loop, for one vertex v of the working set: with the local
+// excess ex and d' = d(v), repeat passes over the residual arcs in order:
+//   admissible  <=> d'(v) = d(w) + 1 (old label of w);
+//   w active and v loses the win rule and the arc is admissible => skip the
+//     arc and end the discharge after this pass;
+//   otherwise push min(res, ex) along an admissible arc;
+//   relabel candidate: d(w) + 1 over arcs still residual with d(w) >= d'(v).
+// After a pass: stop when ex = 0 or an arc was skipped; else d' := candidate
+// minimum (starting at n), work += deg + beta, stop when d' = n.
+
+// Excess delta reaches w: the sink (label 0) accumulates it in a register of
+// the caller, a vertex being discharged this round gets it in addedExcess,
+// any other vertex directly in its excess. Returns true when w must join the
+// next working set through this call (first discovery this round).
+__device__ __forceinline__ bool deliver(const Dev &D, int w, int dw, bool w_active, long long delta, int r) {
+  if (w_active)
+    atomicAdd(reinterpret_cast<unsigned long long *>(&D.added[w]), (unsigned long long)delta);
+  else
+    atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[w]), (unsigned long long)delta);
+  return atomicExch(&D.disc[w], r) != r;
+}
+
+__device__ __forceinline__ void finish_vertex(const Dev &D, int v, int dp, long long ex, int cap_v, int r,
+                                              int *next, int *next_cnt) {
+  D.dn[v] = dp;
+  D.e[v] = ex;
+  if (ex > 0 && dp < cap_v) {
+    if (atomicExch(&D.disc[v], r) != r) append(D, next, next_cnt, v);
+  }
+}
+
+// Sink deliveries of one lane are summed in `to_sink`; lanes that delivered
+// to the same sink combine into one atomic.
+__device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_sink) {
+  if (sink < 0) return;
+  cg::coalesced_group g = cg::coalesced_threads();
+  cg::coalesced_group part = cg::labeled_partition(g, sink);
+  const long long sum = cg::reduce(part, to_sink, cg::plus<long long>());
+  if (part.thread_rank() == 0)
+    atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[sink]), (unsigned long long)sum);
+}
+
+// One thread, deg <= KT: arcs cached in registers for all passes.
+__device__ void discharge_thread(const Dev &D, int v, int beg, int deg, int r, int *next, int *next_cnt,
+                                 TStat &st, long long &work) {
+  int wv[KT], rs[KT], dw[KT];
+  unsigned act = 0;
+#pragma unroll
+  for (int i = 0; i < KT; i++) {
+    wv[i] = 0;
+    rs[i] = 0;
+    dw[i] = 0;
+    if (i < deg) {
+      wv[i] = __ldg(&D.head[beg + i]);
+      rs[i] = __ldcg(&D.rr[beg + i]).x;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KT; i++)
+    if (rs[i] > 0) {
+      const int2 x = __ldcg(&D.vl[wv[i]]);
+      dw[i] = x.x;
+      if (x.y == r) act |= 1u << i;
+    }
+  const int2 me = __ldcg(&D.vl[v]);
+  const int dv = me.x;
+  const int cap_v = cap_of(D, v);
+  long long ex = __ldcg(&D.e[v]);
+  int dp = dv;
+  long long to_sink = 0;
+  int sink = -1;
+  unsigned found = 0;
+  for (;;) {
+    int newl = cap_v;
+    bool skipped = false;
+#pragma unroll
+    for (int i = 0; i < KT; i++) {
+      if (i < deg && ex > 0 && rs[i] > 0) {
+        st.scans_dis++;
+        const bool adm = (dp == dw[i] + 1);
+        if (adm && ((act >> i) & 1u) && !wins(dv, dw[i], v, wv[i])) {
+          skipped = true;
+        } else {
+          if (adm) {
+            const long long delta = rs[i] < ex ? (long long)rs[i] : ex;
+            push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+            rs[i] -= (int)delta;
+            ex -= delta;
+            st.pushes++;
+            if (dw[i] == 0) {
+              to_sink += delta;
+              sink = wv[i];
+            } else if (deliver(D, wv[i], dw[i], (act >> i) & 1u, delta, r)) {
+              found |= 1u << i;
+            }
+          }
+          if (rs[i] > 0 && dw[i] >= dp) newl = min(newl, dw[i] + 1);
+        }
+      }
+    }
+    if (ex == 0 || skipped) break;
+    dp = newl;
+    st.relabels++;
+    work += deg + D.beta;
+    if (dp >= cap_v) break;
+  }
+  finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+#pragma unroll
+  for (int i = 0; i < KT; i++)
+    if ((found >> i) & 1u) append(D, next, next_cnt, wv[i]);
+  flush_sink(D, sink, to_sink);
+}
+
+// One warp (all 32 lanes call), arcs in chunks of 32.
+__device__ void discharge_warp(const Dev &D, int v, int r, int *next, int *next_cnt, TStat &st, long long &work) {
+  const int lane = threadIdx.x & 31;
+  const int beg = __ldg(&D.row[v]);
+  const int deg = __ldg(&D.row[v + 1]) - beg;
+  const int dv = __ldcg(&D.vl[v]).x;
+  const int cap_v = cap_of(D, v);
+  long long ex = __ldcg(&D.e[v]);
+  int dp = dv;
+  long long to_sink = 0;
+  int sink = -1;
+  for (;;) {
+    int newl = cap_v;
+    bool skipped = false;
+    for (int c = 0; c < deg && ex > 0; c += 32) {
+      const int i = c + lane;
+      int w = 0, rs = 0, dw = 0;
+      bool wact = false;
+      if (i < deg) {
+        w = __ldg(&D.head[beg + i]);
+        rs = __ldcg(&D.rr[beg + i]).x;
+        if (rs > 0) {
+          int2 x = __ldcg(&D.vl[w]);
+          dw = x.x;
+          wact = (x.y == r);
+        }
+      }
+      const bool resid = rs > 0;
+      const bool adm = resid && dp == dw + 1;
+      const bool skip = adm && wact && !wins(dv, dw, v, w);
+      const bool pushable = adm && !skip;
+      const long long pr = pushable ? (long long)rs : 0;
+      const long long incl = warp_incl_scan(pr, lane);
+      const long long excl = incl - pr;
+      const long long total = __shfl_sync(FULL, incl, 31);
+      long long delta = 0;
+      if (pushable && excl < ex) delta = min((long long)rs, ex - excl);
+      st.scans_dis += (resid ? 1 : 0);
+      bool found = false;
+      if (delta > 0) {
+        push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+        rs -= (int)delta;
+        st.pushes++;
+        if (dw == 0) {
+          to_sink += delta;
+          sink = w;
+        } else {
+          found = deliver(D, w, dw, wact, delta, r);
+        }
+      }
+      if (found) append(D, next, next_cnt, w);
+      if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
+      skipped |= (__ballot_sync(FULL, skip) != 0);
+      ex = total >= ex ? 0 : ex - total;
+    }
+    newl = warp_min(newl);
+    if (ex == 0 || skipped) break;
+    dp = newl;
+    if (lane == 0) {
+      st.relabels++;
+      work += deg + D.beta;
+    }
+    if (dp >= cap_v) break;
+  }
+  if (lane == 0) finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+  __syncwarp();
+  if (sink >= 0) flush_sink(D, sink, to_sink);
+  __syncwarp();
+}
+
+// One CTA (all threads call), arcs in chunks of blockDim.
+__device__ void discharge_block(const Dev &D, int v, int r, int *next, int *next_cnt, TStat &st, long long &work,
+                                Shared &sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int beg = __ldg(&D.row[v]);
+  const int deg = __ldg(&D.row[v + 1]) - beg;
+  const int dv = __ldcg(&D.vl[v]).x;
+  const int cap_v = cap_of(D, v);
+  long long ex = __ldcg(&D.e[v]);
+  int dp = dv;
+  long long to_sink = 0;
+  int sink = -1;
+  for (;;) {
+    int newl = cap_v;
+    int skipped = 0;
+    for (int c = 0; c < deg && ex > 0; c += blockDim.x) {
+      const int i = c + threadIdx.x;
+      int w = 0, rs = 0, dw = 0;
+      bool wact = false;
+      if (i < deg) {
+        w = __ldg(&D.head[beg + i]);
+        rs = __ldcg(&D.rr[beg + i]).x;
+        if (rs > 0) {
+          int2 x = __ldcg(&D.vl[w]);
+          dw = x.x;
+          wact = (x.y == r);
+        }
+      }
+      const bool resid = rs > 0;
+      const bool adm = resid && dp == dw + 1;
+      const bool skip = adm && wact && !wins(dv, dw, v, w);
+      const bool pushable = adm && !skip;
+      const long long pr = pushable ? (long long)rs : 0;
+      const long long incl_w = warp_incl_scan(pr, lane);
+      __syncthreads();  // previous chunk finished reading sh
+      if (lane == 31) sh.lsum[wid] = incl_w;
+      if (threadIdx.x == 0) sh.flag = 0;
+      __syncthreads();
+      long long wbase = 0, total = 0;
+      for (int k = 0; k < nw; k++) {
+        long long s = sh.lsum[k];
+        if (k < wid) wbase += s;
+        total += s;
+      }
+      const long long excl = wbase + incl_w - pr;
+      long long delta = 0;
+      if (pushable && excl < ex) delta = min((long long)rs, ex - excl);
+      st.scans_dis += (resid ? 1 : 0);
+      bool found = false;
+      if (delta > 0) {
+        push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+        rs -= (int)delta;
+        st.pushes++;
+        if (dw == 0) {
+          to_sink += delta;
+          sink = w;
+        } else {
+          found = deliver(D, w, dw, wact, delta, r);
+        }
+      }
+      if (found) append(D, next, next_cnt, w);
+      if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
+      if (skip) sh.flag = 1;
+      __syncthreads();
+      skipped |= sh.flag;
+      ex = total >= ex ? 0 : ex - total;
+    }
+    // block min of newl
+    int wm = warp_min(newl);
+    __syncthreads();
+    if (lane == 0) sh.imin[wid] = wm;
+    __syncthreads();
+    newl = cap_v;
+    for (int k = 0; k < nw; k++) newl = min(newl, sh.imin[k]);
+    if (ex == 0 || skipped) break;
+    dp = newl;
+    if (threadIdx.x == 0) {
+      st.relabels++;
+      work += deg + D.beta;
+    }
+    if (dp >= cap_v) break;
+  }
+  if (threadIdx.x == 0) finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+  if (sink >= 0) flush_sink(D, sink, to_sink);
+  __syncthreads();
+}
+
+// Discharge every vertex of list generation `gen`; discoveries go to gen + 1.
+__device__ void discharge_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd, TStat &st) {
+  const int *W = D.list[gen & 1];
+  int *next = D.list[(gen + 1) & 1];
+  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  const int count = list_count(D, gen);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) % 3] = 0;
+    D.ctl->live[(gen + 2) % 3] = 0;
+  }
+  const int lane = threadIdx.x & 31;
+  long long work = 0;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+    const int idx = base + threadIdx.x;
+    int v = idx < count ? __ldcg(&W[idx]) : -1;
+    int beg = 0, deg = 0, cls = 0;
+    if (v >= 0) {
+      beg = __ldg(&D.row[v]);
+      deg = __ldg(&D.row[v + 1]) - beg;
+      cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
+      st.visits_dis++;
+    }
+    for (;;) {  // CTA per vertex
+      if (threadIdx.x == 0) sh.pick = -1;
+      __syncthreads();
+      if (cls == 3) sh.pick = v;
+      __syncthreads();
+      const int pv = sh.pick;
+      if (pv < 0) break;
+      if (v == pv) cls = 0;
+      discharge_block(D, pv, r, next, next_cnt, st, work, sh);
+    }
+    for (;;) {  // warp per vertex
+      const unsigned mm = __ballot_sync(FULL, cls == 2);
+      if (!mm) break;
+      const int leader = __ffs(mm) - 1;
+      const int pv = __shfl_sync(FULL, v, leader);
+      if (lane == leader) cls = 0;
+      discharge_warp(D, pv, r, next, next_cnt, st, work);
+    }
+    if (cls == 1) discharge_thread(D, v, beg, deg, r, next, next_cnt, st, work);
+    __syncwarp();
+  }
+  const long long wsum = block_sum(work, sh);
+  if (threadIdx.x == 0 && wsum) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->work[rnd & 1]),
+                                          (unsigned long long)wsum);
+}
+
+// Algorithm 1 after the discharge: old working set takes d := d' and its
+// addedExcess; the new list keeps the vertices whose label (d' if they were
+// discharged) is below the cap and stamps them active for round r + 1.
+__device__ void apply_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int *W = D.list[gen & 1];
+  int *N = D.list[(gen + 1) & 1];
+  const int cw = list_count(D, gen);
+  const int cn = list_count(D, gen + 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->work[(rnd + 1) & 1] = 0;
+  for (int i = tid; i < cw; i += nthr) {
+    const int v = __ldcg(&W[i]);
+    if (v < 0) continue;
+    *label_ptr(D, v) = __ldcg(&D.dn[v]);
+    const long long ad = __ldcg(&D.added[v]);
+    if (ad) {
+      D.e[v] = __ldcg(&D.e[v]) + ad;
+      D.added[v] = 0;
+    }
+  }
+  int live = 0;
+  for (int i = tid; i < cn; i += nthr) {
+    const int u = __ldcg(&N[i]);
+    const int2 x = __ldcg(&D.vl[u]);
+    const int de = (x.y == r) ? __ldcg(&D.dn[u]) : x.x;
+    if (de < cap_of(D, u)) {
+      *stamp_ptr(D, u) = r + 1;
+      live++;
+    } else {
+      N[i] = -1;
+    }
+  }
+  const long long ls = block_sum(live, sh);
+  if (threadIdx.x == 0 && ls) atomicAdd(&D.ctl->live[(gen + 1) % 3], (int)ls);
+}
+
+// ------------------------------------------------------------------ BFS
+//
+// Level-synchronous BFS (Algorithm 2). A frontier vertex v at level k
+// discovers w through slot a = (v -> w) when the tested residual is positive
+// (reverse BFS for the global relabel: res[rev[a]] = c_f(w, v); forward BFS for
+// the cut: res[a] = c_f(v, w)) and CAS(label(w): UNV -> k + 1) succeeds.
+
+__device__ __forceinline__ void bfs_arc(const Dev &D, int a, int lvl, bool reverse, int *next, int *next_cnt) {
+  const int w = __ldg(&D.head[a]);
+  const int2 x = __ldcg(&D.rr[a]);
+  const int cf = reverse ? x.y : x.x;
+  if (cf > 0 && __ldcg(label_ptr(D, w)) == UNV) {
+    if (atomicCAS(label_ptr(D, w), UNV, lvl + 1) == UNV) append(D, next, next_cnt, w);
+  }
+}
+
+// One thread, deg <= KT, loads issued together.
+__device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int lvl, bool reverse, int *next,
+                                           int *next_cnt) {
+  int w[KT], cf[KT], lab[KT];
+#pragma unroll
+  for (int i = 0; i < KT; i++) {
+    w[i] = 0;
+    cf[i] = 0;
+    if (i < deg) {
+      w[i] = __ldg(&D.head[beg + i]);
+      const int2 x = __ldcg(&D.rr[beg + i]);
+      cf[i] = reverse ? x.y : x.x;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(label_ptr(D, w[i])) : 0;
+#pragma unroll
+  for (int i = 0; i < KT; i++)
+    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(label_ptr(D, w[i]), UNV, lvl + 1) == UNV)
+      append(D, next, next_cnt, w[i]);
+}
+
+__device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
+  const int *F = D.list[gen & 1];
+  int *next = D.list[(gen + 1) & 1];
+  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  const int count = list_count(D, gen);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) % 3] = 0;
+    D.ctl->live[(gen + 2) % 3] = 0;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const int v = idx < count ? __ldcg(&F[idx]) : -1;
+    int beg = 0, deg = 0, cls = 0;
+    if (v >= 0) {
+      beg = __ldg(&D.row[v]);
+      deg = __ldg(&D.row[v + 1]) - beg;
+      cls = deg <= KT ? 1 : (deg <= D.bin_warp ? 2 : 3);
+      st.scans_bfs += deg;
+      st.visits_bfs++;
+    }
+    for (;;) {
+      if (threadIdx.x == 0) sh.pick = -1;
+      __syncthreads();
+      if (cls == 3) sh.pick = v;
+      __syncthreads();
+      const int pv = sh.pick;
+      if (pv < 0) break;
+      if (v == pv) cls = 0;
+      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, a, lvl, reverse, next, next_cnt);
+      __syncthreads();
+    }
+    for (;;) {
+      const unsigned mm = __ballot_sync(FULL, cls == 2);
+      if (!mm) break;
+      const int leader = __ffs(mm) - 1;
+      const int pv = __shfl_sync(FULL, v, leader);
+      if (lane == leader) cls = 0;
+      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      for (int a = b + lane; a < e; a += 32) bfs_arc(D, a, lvl, reverse, next, next_cnt);
+      __syncwarp();
+    }
+    if (cls == 1) bfs_thread(D, beg, deg, lvl, reverse, next, next_cnt);
+    __syncwarp();
+  }
+}
+
+// BFS from `seeds` (label 0). `blockers` get UNV + 1 and are never reached.
+// With `excess_seeds`, every vertex holding excess whose label lies in
+// [1, cap] is a seed as well (cut from the maximum preflow). Returns false on
+// error. On return the last list generation is empty.
+__device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *blockers, int nterm, bool reverse,
+                    bool excess_seeds, int &gen, TStat &st, int where) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  int *next = D.list[(gen + 1) & 1];
+  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  // phase A: every label to UNV (excess-holding non-terminals become seeds)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) % 3] = 0;
+    D.ctl->live[(gen + 2) % 3] = 0;
+  }
+  for (int v = tid; v < D.n; v += nthr) {
+    int x = UNV;
+    if (excess_seeds) {
+      const int d = __ldcg(label_ptr(D, v));
+      if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) > 0) {
+        x = 0;
+        append(D, next, next_cnt, v);
+      }
+    }
+    *label_ptr(D, v) = x;
+  }
+  if (!grid_sync(D, sh, where)) return false;
+  // phase B: terminals (seeds join generation gen + 1 as well)
+  for (int i = tid; i < nterm; i += nthr) {
+    *label_ptr(D, seeds[i]) = 0;
+    if (blockers) *label_ptr(D, blockers[i]) = UNV + 1;
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < nterm; i += blockDim.x) {
+      int x = seeds[i];
+      append(D, next, next_cnt, x);
+    }
+  }
+  if (!grid_sync(D, sh, where)) return false;
+  gen++;
+  // excess seeds may repeat a terminal seed; a repeat only rescans its arcs
+  for (int lvl = 0;; lvl++) {
+    if (__ldcg(&D.ctl->cnt[gen % 3]) == 0) break;
+    bfs_level(D, sh, gen, lvl, reverse, st);
+    if (!grid_sync(D, sh, where)) return false;
+    gen++;
+    if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->levels++;
+  }
+  return true;
+}
+
+// Global relabel (Algorithm 2 from the sinks, never entering the sources),
+// then the working set is rebuilt for round r: labels left at UNV become the
+// cap n, sources n + 1, and every vertex with excess and 0 < d < n is
+// stamped active. Result: list generation gen.
+__device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const int *sources, int r, int &gen,
+                               TStat &st) {
+  if (!bfs(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2)) return false;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  int *next = D.list[(gen + 1) & 1];
+  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) % 3] = 0;
+    D.ctl->live[(gen + 2) % 3] = 0;
+    D.ctl->grs++;
+  }
+  int live = 0;
+  for (int v = tid; v < D.n; v += nthr) {
+    const int x = __ldcg(label_ptr(D, v));
+    const int c = cap_of(D, v);
+    const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
+    if (d != x) *label_ptr(D, v) = d;
+    if (d > 0 && d < c && __ldcg(&D.e[v]) > 0) {
+      *stamp_ptr(D, v) = r;
+      append(D, next, next_cnt, v);
+      live++;
+    }
+  }
+  const long long ls = block_sum(live, sh);
+  if (threadIdx.x == 0 && ls) atomicAdd(&D.ctl->live[(gen + 1) % 3], (int)ls);
+  if (!grid_sync(D, sh, 3)) return false;
+  gen++;
+  return true;
+}
+
+// Rounds of Algorithm 1 toward `sinks` until no vertex is active right after a
+// global relabel (or, in MODE_ROUNDS, until stop_rounds rounds ran).
+__device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int *sources, int &r, int &gen,
+                          long long &rnd, bool phase1, TStat &st) {
+  long long since_gr = LLONG_MAX;
+  bool fresh = false;
+  long long rounds = 0;
+  for (;;) {
+    if (since_gr > D.gr_threshold) {
+      r++;  // fresh stamp: marks of the discarded working set are stale
+      if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+      since_gr = 0;
+      fresh = true;
+    }
+    const int live = __ldcg(&D.ctl->live[gen % 3]);
+    if (live == 0) {
+      if (fresh) break;
+      since_gr = LLONG_MAX;
+      continue;
+    }
+    if (D.mode == MODE_ROUNDS && rounds >= D.stop_rounds) break;
+    if (rounds >= D.max_rounds) {
+      set_err(D, MF_ERR_ITER_LIMIT, 10);
+      return false;
+    }
+    fresh = false;
+    discharge_phase(D, sh, r, gen, rnd, st);
+    if (!grid_sync(D, sh, 4)) return false;
+    apply_phase(D, sh, r, gen, rnd);
+    if (!grid_sync(D, sh, 5)) return false;
+    since_gr += __ldcg(&D.ctl->work[rnd & 1]);
+    r++;
+    gen++;
+    rnd++;
+    rounds++;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      D.ctl->rounds++;
+      if (phase1) D.ctl->rounds_phase1++;
+    }
+  }
+  if (D.mode == MODE_ROUNDS) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->stopped_round = (int)rounds;
+    if (D.final_gr) {
+      r++;
+      if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ kernel
+
+__global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
+  __shared__ Shared sh;
+  if (threadIdx.x == 0) sh.gen = 0;
+  __syncthreads();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  TStat st;
+  if (tid == 0) D.ctl->t_start = gtimer();
+
+  // Initialisation (Algorithm 1): residuals from the capacities, labels 0,
+  // excess 0, no stamps.
+  for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
+  for (int v = tid; v < D.n; v += nthr) {
+    D.vl[v] = make_int2(0, -1);
+    D.dn[v] = 0;
+    D.e[v] = 0;
+    D.added[v] = 0;
+    D.disc[v] = -1;
+  }
+  bool ok = grid_sync(D, sh, 0);
+  // Saturate every arc out of each source (self-loops excluded).
+  if (ok) {
+    for (int k = 0; k < D.ninst; k++) {
+      const int s = D.src[k];
+      const int b = __ldg(&D.row[s]), e = __ldg(&D.row[s + 1]);
+      for (int a = b + tid; a < e; a += nthr) {
+        const int c = __ldg(&D.cap[a]);
+        const int w = __ldg(&D.head[a]);
+        if (c <= 0 || w == s) continue;
+        const int ra = __ldg(&D.rev[a]);
+        const int cr = __ldg(&D.cap[ra]);
+        D.rr[a] = make_int2(0, cr + c);
+        D.rr[ra] = make_int2(cr + c, 0);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[w]), (unsigned long long)(long long)c);
+      }
+    }
+    ok = grid_sync(D, sh, 1);
+  }
+  int r = 0, gen = 0;
+  long long rnd = 0;
+  if (ok) ok = run_phase(D, sh, D.snk, D.src, r, gen, rnd, true, st);
+  if (ok && D.mode == MODE_SOLVE) {
+    if (tid == 0) D.ctl->t_preflow = gtimer();
+    for (int k = tid; k < D.ninst; k += nthr) {
+      const long long val = __ldcg(&D.e[D.snk[k]]);
+      if (D.out_value) D.out_value[k] = val;
+      if (k == 0) D.ctl->value = val;
+    }
+    if (D.cut_only) {
+      // S_min from the maximum preflow: reachable from s and every excess vertex.
+      ok = bfs(D, sh, D.src, nullptr, D.ninst, false, true, gen, st, 6);
+    } else {
+      // Phase 2: return the excess that cannot reach t to s (s plays the sink).
+      ok = run_phase(D, sh, D.src, D.snk, r, gen, rnd, false, st);
+      if (ok) {
+        long long left = 0;
+        for (int v = tid; v < D.n; v += nthr) {
+          const int d = __ldcg(label_ptr(D, v));
+          if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) != 0) left++;
+        }
+        left = block_sum(left, sh);
+        if (threadIdx.x == 0 && left) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->leftover),
+                                                (unsigned long long)left);
+        ok = grid_sync(D, sh, 7);
+        if (ok && __ldcg(&D.ctl->leftover) != 0) {
+          set_err(D, MF_ERR_INTERNAL, 8);
+          ok = false;
+        }
+      }
+      // Cut: BFS from s over arcs with positive residual.
+      if (ok) ok = bfs(D, sh, D.src, nullptr, D.ninst, false, false, gen, st, 9);
+    }
+    if (ok) {
+      if (D.out_cut) {
+        const int words = (D.n + 31) >> 5;
+        for (int wd = tid; wd < words; wd += nthr) {
+          unsigned bits = 0;
+          for (int j = 0; j < 32; j++) {
+            const int v = wd * 32 + j;
+            if (v < D.n && __ldcg(label_ptr(D, v)) != UNV) bits |= 1u << j;
+          }
+          D.out_cut[wd] = bits;
+        }
+      }
+      if (D.out_flow)
+        for (int a = tid; a < D.m; a += nthr) {
+          const int f = __ldg(&D.cap[a]) - __ldcg(&D.rr[a]).x;
+          D.out_flow[a] = f > 0 ? f : 0;
+        }
+    }
+  }
+  // statistics
+  long long x;
+  x = block_sum(st.scans_dis, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->scans_dis), (unsigned long long)x);
+  x = block_sum(st.scans_bfs, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->scans_bfs), (unsigned long long)x);
+  x = block_sum(st.pushes, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->pushes), (unsigned long long)x);
+  x = block_sum(st.relabels, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->relabels), (unsigned long long)x);
+  x = block_sum(st.visits_dis, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->visits_dis), (unsigned long long)x);
+  x = block_sum(st.visits_bfs, sh);
+  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->visits_bfs), (unsigned long long)x);
+  if (tid == 0) D.ctl->t_end = gtimer();
+}
+
+// ------------------------------------------------------------------ host side
+
+int solver_occupancy(int block_threads, int *blocks_per_sm) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block_threads, 0);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream) {
+  Dev d = D;
+  void *args[] = {&d};
+  return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args, 0, stream);
+}
+
+}  // namespace mf

@@ -1,0 +1,265 @@
+"""Python binding of libmf (include/mf.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA kernels of ``libmf.so``; this module converts numpy arrays or
+torch tensors to pointers and raises ``MFError`` on a non-zero status. If ``libmf.so`` has not been
+built, importing the library fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_OK, MF_PENDING = 0, 1
+ERR_NAMES = {-1: "MF_ERR_INVALID_ARG", -2: "MF_ERR_BAD_PAIRING", -3: "MF_ERR_S_EQ_T", -4: "MF_ERR_CAP_OVERFLOW",
+             -5: "MF_ERR_OOM", -6: "MF_ERR_OVER_BUDGET", -7: "MF_ERR_ITER_LIMIT", -8: "MF_ERR_TIMEOUT",
+             -9: "MF_ERR_CUDA", -10: "MF_ERR_INTERNAL", -11: "MF_ERR_TOO_LARGE", -12: "MF_ERR_UNKNOWN_TICKET"}
+
+
+class MFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("gr_freq", ctypes.c_double), ("gr_alpha", ctypes.c_int32), ("work_beta", ctypes.c_int32),
+                ("bin_thread", ctypes.c_int32), ("bin_warp", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int32),
+                ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("rounds_phase1", ctypes.c_int64), ("global_relabels", ctypes.c_int64),
+                ("bfs_levels", ctypes.c_int64), ("scans_discharge", ctypes.c_int64), ("scans_bfs", ctypes.c_int64),
+                ("pushes", ctypes.c_int64), ("relabels", ctypes.c_int64), ("visits_discharge", ctypes.c_int64),
+                ("visits_bfs", ctypes.c_int64), ("solve_ms", ctypes.c_double),
+                ("preflow_ms", ctypes.c_double), ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("row_offsets", ctypes.POINTER(ctypes.c_int64)),
+                ("head", ctypes.POINTER(ctypes.c_int32)), ("cap", ctypes.POINTER(ctypes.c_int32)),
+                ("rev", ctypes.POINTER(ctypes.c_int64)), ("arc_slot", ctypes.POINTER(ctypes.c_int64)),
+                ("dropped_self_loops", ctypes.c_int64)]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("row_offsets", ctypes.c_void_p),
+                ("head", ctypes.c_void_p), ("cap", ctypes.c_void_p), ("rev", ctypes.c_void_p),
+                ("s", ctypes.c_int32), ("t", ctypes.c_int32)]
+
+
+_lib = None
+EXPORTS = ["mf_default_options", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
+           "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
+           "mf_destroy_graph"]
+
+
+def lib():
+    """Loads libmf.so (raises OSError if it is missing or cannot be loaded)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.mf_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.mf_default_options.restype = None
+        L.mf_last_error.restype = ctypes.c_char_p
+        L.mf_build_csr.argtypes = [i32, i64, vp, vp, vp, ctypes.POINTER(_CSR)]
+        L.mf_free_csr.argtypes = [ctypes.POINTER(_CSR)]
+        L.mf_free_csr.restype = None
+        L.mf_create_graph.argtypes = [i32, i64, vp, vp, vp, vp, i32, i32, ctypes.POINTER(Options),
+                                      ctypes.POINTER(vp)]
+        L.mf_create_graph_device.argtypes = [i32, i64, vp, vp, vp, vp, i32, i32, ctypes.POINTER(Options), vp,
+                                             ctypes.POINTER(vp)]
+        L.mf_solve.argtypes = [vp, vp, vp, vp]
+        L.mf_solve_device.argtypes = [vp, vp, vp, vp, vp]
+        L.mf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.mf_run_rounds.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+        L.mf_destroy_graph.argtypes = [vp]
+        L.mf_destroy_graph.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise MFError(rc, lib().mf_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    lib().mf_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class CSR:
+    """Paired-slot CSR (see include/mf.h)."""
+
+    n: int
+    row_offsets: np.ndarray  # int64[n+1]
+    head: np.ndarray         # int32[m]
+    cap: np.ndarray          # int32[m]
+    rev: np.ndarray          # int64[m]
+    arc_slot: np.ndarray     # int64[m_in]
+    dropped_self_loops: int
+
+    @property
+    def m(self) -> int:
+        return int(self.head.shape[0])
+
+    def tails(self) -> np.ndarray:
+        return np.repeat(np.arange(self.n, dtype=np.int32), np.diff(self.row_offsets))
+
+
+def build_csr(n, tail, head, cap) -> CSR:
+    tail = np.ascontiguousarray(tail, np.int32)
+    head = np.ascontiguousarray(head, np.int32)
+    cap = np.ascontiguousarray(cap, np.int32)
+    c = _CSR()
+    _check(lib().mf_build_csr(n, tail.shape[0], _ptr(tail), _ptr(head), _ptr(cap), ctypes.byref(c)))
+    try:
+        m = int(c.m)
+
+        def grab(p, k):
+            return np.ctypeslib.as_array(p, shape=(k,)).copy() if k else np.zeros(0, p._type_)
+
+        return CSR(n, grab(c.row_offsets, n + 1), grab(c.head, m), grab(c.cap, m), grab(c.rev, m),
+                   grab(c.arc_slot, tail.shape[0]), int(c.dropped_self_loops))
+    finally:
+        lib().mf_free_csr(ctypes.byref(c))
+
+
+def cut_bits_to_bool(bits, n) -> np.ndarray:
+    b = np.asarray(bits, dtype=np.uint32).view(np.uint8)
+    return np.unpackbits(b, bitorder="little")[:n].astype(bool)
+
+
+@dataclass
+class Result:
+    value: int
+    flow: np.ndarray | None      # int32[m] per slot
+    cut_bits: np.ndarray | None  # uint32[ceil(n/32)]
+
+
+class Graph:
+    """A max-flow instance resident on the GPU (mf_create_graph / mf_solve)."""
+
+    def __init__(self, n, row_offsets, head, cap, rev, s, t, options: Options | None = None, _handle=None):
+        self.n, self.s, self.t = int(n), int(s), int(t)
+        self._h = ctypes.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+            self.m = int(head.shape[0]) if head is not None else 0
+            return
+        row_offsets = np.ascontiguousarray(row_offsets, np.int64)
+        head = np.ascontiguousarray(head, np.int32)
+        cap = np.ascontiguousarray(cap, np.int32)
+        rev = np.ascontiguousarray(rev, np.int64)
+        self.m = int(head.shape[0])
+        _check(lib().mf_create_graph(self.n, self.m, _ptr(row_offsets), _ptr(head), _ptr(cap), _ptr(rev), self.s,
+                                     self.t, ctypes.byref(options) if options else None, ctypes.byref(self._h)))
+
+    @classmethod
+    def from_csr(cls, csr: CSR, s, t, options: Options | None = None) -> "Graph":
+        return cls(csr.n, csr.row_offsets, csr.head, csr.cap, csr.rev, s, t, options)
+
+    @classmethod
+    def from_device(cls, n, row_offsets, head, cap, rev, s, t, options: Options | None = None, stream=None):
+        """From torch CUDA tensors (int64 row_offsets/rev, int32 head/cap)."""
+        h = ctypes.c_void_p()
+        m = int(head.shape[0])
+        _check(lib().mf_create_graph_device(int(n), m, _ptr(row_offsets), _ptr(head), _ptr(cap), _ptr(rev), int(s),
+                                            int(t), ctypes.byref(options) if options else None,
+                                            _stream_ptr(stream), ctypes.byref(h)))
+        g = cls(n, None, head, None, None, s, t, _handle=h)
+        return g
+
+    def solve(self, flow=True, cut=True) -> Result:
+        v = ctypes.c_int64()
+        f = np.zeros(self.m, np.int32) if flow else None
+        c = np.zeros((self.n + 31) // 32, np.uint32) if cut else None
+        _check(lib().mf_solve(self._h, ctypes.byref(v), _ptr(f), _ptr(c)))
+        return Result(int(v.value), f, c)
+
+    def solve_device(self, value=None, flow=None, cut_bits=None, stream=None):
+        """Outputs into torch CUDA tensors (int64[1], int32[m], int32/uint32[ceil(n/32)]), each optional."""
+        _check(lib().mf_solve_device(self._h, _stream_ptr(stream), _ptr(value), _ptr(flow), _ptr(cut_bits)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().mf_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def run_rounds(self, rounds: int, final_relabel: bool = True):
+        """Phase-1 state after `rounds` rounds: (residual int32[m], label int32[n], excess int64[n], rounds)."""
+        res = np.zeros(self.m, np.int32)
+        lab = np.zeros(self.n, np.int32)
+        ex = np.zeros(self.n, np.int64)
+        done = ctypes.c_int64()
+        _check(lib().mf_run_rounds(self._h, int(rounds), 1 if final_relabel else 0, _ptr(res), _ptr(lab), _ptr(ex),
+                                   ctypes.byref(done)))
+        return res, lab, ex, int(done.value)
+
+    def close(self):
+        if self._h:
+            lib().mf_destroy_graph(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_instance(inst, options: Options | None = None, flow=True, cut=True):
+    """Builds the CSR of an input arc list (tail/head/cap arrays, n, s, t) and solves it on the GPU.
+    Returns (value, per-input-arc flow int64 or None, cut bool[n] or None, csr, stats)."""
+    csr = build_csr(inst.n, inst.tail, inst.head, inst.cap)
+    with Graph.from_csr(csr, inst.s, inst.t, options) as g:
+        r = g.solve(flow=flow, cut=cut)
+        st = g.stats()
+    fin = None
+    if flow:
+        fin = np.where(csr.arc_slot >= 0, r.flow[np.maximum(csr.arc_slot, 0)], 0).astype(np.int64)
+    cut_b = cut_bits_to_bool(r.cut_bits, inst.n) if cut else None
+    return r.value, fin, cut_b, csr, st
