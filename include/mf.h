@@ -83,6 +83,12 @@ typedef struct mf_options {
   int32_t cut_only;
   /* CUDA device ordinal the graph lives on. */
   int32_t device;
+  /* Additional global-relabel trigger (0 = off; default 2): relabel when the
+   * time spent in rounds since the last global relabel exceeds gr_time_ratio
+   * times the time that relabel took. On a GPU a round costs about as much as
+   * a few BFS levels whatever its size, so the work-based trigger alone lets
+   * a few trapped vertices climb to n one round at a time. */
+  double gr_time_ratio;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
@@ -100,6 +106,9 @@ typedef struct mf_stats {
   int64_t visits_bfs;       /* frontier entries expanded */
   double solve_ms;          /* device time of the whole solve (CUDA events) */
   double preflow_ms;        /* device time to the maximum preflow */
+  double relabel_ms;        /* time in global relabels (BFS + working-set rebuild) */
+  double discharge_ms;      /* time in push-relabel rounds */
+  int64_t rounds_by_size[4]; /* rounds whose working set had <1K, <16K, <256K, more vertices */
   int32_t grid_blocks;      /* persistent-kernel CTAs */
   int32_t block_threads;
 } mf_stats;
@@ -179,6 +188,12 @@ int mf_solve(mf_graph *g, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_
  * returns after the solve finished (it reads the status word back). */
 int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d_arc_flow, uint32_t *d_cut_bits);
 
+/* Tracing: solves g like mf_solve (no outputs) and records, for each of the
+ * first `capacity` push-relabel rounds of both phases, the working-set size
+ * (live[k]) and whether a global relabel ran right before the round
+ * (relabel_before[k] = 1). *rounds = total rounds (may exceed capacity). */
+int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds);
+
 /* Counters of the last solve on g. */
 int mf_get_stats(const mf_graph *g, mf_stats *out);
 
@@ -194,6 +209,20 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
                   int64_t *excess, int64_t *rounds_done);
 
 void mf_destroy_graph(mf_graph *g);
+
+/*
+ * Batched solving: `count` independent instances (host descriptions, copied)
+ * packed into one device graph (instance-offset CSR) and solved by one
+ * persistent launch; every instance keeps its own n, s, t and label cap, and
+ * takes part in a round only while it has active vertices. values[i] = flow
+ * value of instance i; arc_flows[i] / cut_bits[i] (each entry nullable, and the
+ * pointer arrays themselves nullable) as for mf_solve, in instance-local
+ * numbering. The union must stay below 2^30 vertices and 2^31 slots.
+ */
+int mf_batch_create(int32_t count, const mf_graph_desc *descs, const mf_options *opt, mf_batch **out);
+int mf_batch_solve(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits);
+int mf_batch_get_stats(const mf_batch *b, mf_stats *out);
+void mf_batch_destroy(mf_batch *b);
 
 #ifdef __cplusplus
 }

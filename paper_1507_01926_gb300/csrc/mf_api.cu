@@ -116,8 +116,8 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vl, g->dn, g->e, g->added, g->disc,
-                g->list[0], g->list[1], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->e, g->added, g->list[0], g->list[1], g->list[2],
+                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -159,13 +159,11 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
   if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
-  if ((rc = dalloc((void **)&g->vl, n * 8, "cudaMalloc labels"))) return rc;
-  if ((rc = dalloc((void **)&g->dn, n * 4, "cudaMalloc d'"))) return rc;
+  if ((rc = dalloc((void **)&g->vs, n * 16, "cudaMalloc vertex state"))) return rc;
   if ((rc = dalloc((void **)&g->e, n * 8, "cudaMalloc excess"))) return rc;
   if ((rc = dalloc((void **)&g->added, n * 8, "cudaMalloc addedExcess"))) return rc;
-  if ((rc = dalloc((void **)&g->disc, n * 4, "cudaMalloc discovery stamps"))) return rc;
-  if ((rc = dalloc((void **)&g->list[0], n * 4, "cudaMalloc list"))) return rc;
-  if ((rc = dalloc((void **)&g->list[1], n * 4, "cudaMalloc list"))) return rc;
+  for (int k = 0; k < 3; k++)
+    if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
   if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
   if ((rc = dalloc((void **)&g->snk, (size_t)g->ninst * 4, "cudaMalloc sinks"))) return rc;
   if ((rc = dalloc((void **)&g->ctl, sizeof(Ctl), "cudaMalloc control block"))) return rc;
@@ -236,6 +234,7 @@ int check_options(const mf_options *o) {
   if (o->gr_alpha < 0 || o->work_beta < 0) return fail(MF_ERR_INVALID_ARG, "gr_alpha, work_beta must be >= 0");
   if (o->timeout_ms <= 0) return fail(MF_ERR_INVALID_ARG, "timeout_ms must be > 0");
   if (o->max_rounds < 0) return fail(MF_ERR_INVALID_ARG, "max_rounds must be >= 0");
+  if (!(o->gr_time_ratio >= 0)) return fail(MF_ERR_INVALID_ARG, "gr_time_ratio must be >= 0");
   return MF_OK;
 }
 
@@ -251,13 +250,10 @@ Dev make_dev(const mf_graph *g) {
   D.rev = g->rev;
   D.cap = g->cap;
   D.rr = g->rr;
-  D.vl = g->vl;
-  D.dn = g->dn;
+  D.vs = g->vs;
   D.e = g->e;
   D.added = g->added;
-  D.disc = g->disc;
-  D.list[0] = g->list[0];
-  D.list[1] = g->list[1];
+  for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
   D.src = g->src;
   D.snk = g->snk;
   D.ninst = g->ninst;
@@ -268,6 +264,7 @@ Dev make_dev(const mf_graph *g) {
   const double thr = ((double)g->opt.gr_alpha * (double)g->n_total_for_gr + (double)g->m_arcs) / g->opt.gr_freq;
   D.gr_threshold = thr > 9.0e18 ? (long long)9e18 : (long long)thr;
   D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
+  D.gr_time_ratio = g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
   D.cut_only = g->opt.cut_only;
@@ -300,14 +297,18 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   s.visits_discharge = c.visits_dis;
   s.visits_bfs = c.visits_bfs;
   s.solve_ms = ms;
+  s.relabel_ms = (double)c.t_gr * 1e-6;
+  s.discharge_ms = (double)c.t_dis * 1e-6;
+  for (int i = 0; i < 4; i++) s.rounds_by_size[i] = c.rounds_by_size[i];
   s.preflow_ms = c.t_preflow > c.t_start ? (double)(c.t_preflow - c.t_start) * 1e-6 : 0.0;
   s.grid_blocks = g->grid;
   s.block_threads = g->block;
   if (c.err) {
     static const char *where[] = {"init barrier", "saturation barrier", "relabel BFS", "working-set rebuild",
                                   "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
-                                  "phase-2 excess check", "cut BFS", "round limit", "list capacity"};
-    const char *w = (c.err_where >= 0 && c.err_where <= 11) ? where[c.err_where] : "?";
+                                  "phase-2 excess check", "cut BFS", "round limit", "list capacity",
+                                  "settle barrier"};
+    const char *w = (c.err_where >= 0 && c.err_where <= 12) ? where[c.err_where] : "?";
     if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
     if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);
     if (c.err == MF_ERR_INTERNAL && c.err_where == 8)
@@ -338,6 +339,7 @@ void mf_default_options(mf_options *o) {
   o->timeout_ms = 5000;
   o->cut_only = 0;
   o->device = 0;
+  o->gr_time_ratio = 2.0;
 }
 
 const char *mf_last_error(void) { return last_error(); }
@@ -489,6 +491,40 @@ int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d
   return solve_into(g, (cudaStream_t)stream, d_flow_value, d_arc_flow, d_cut_bits);
 }
 
+int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds) {
+  clear_error();
+  if (!g || capacity < 0 || (capacity > 0 && (!live || !relabel_before)))
+    return fail(MF_ERR_INVALID_ARG, "bad arguments");
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  int2 *tr = nullptr;
+  if (capacity > 0 && (e = cudaMalloc((void **)&tr, (size_t)capacity * sizeof(int2))) != cudaSuccess)
+    return cuda_fail(e, "cudaMalloc trace");
+  Dev D = make_dev(g);
+  D.out_value = g->d_value;
+  D.trace = tr;
+  D.trace_cap = capacity;
+  int rc = run_kernel(g, D, g->stream);
+  if (rc == MF_OK && capacity > 0) {
+    const long long nr = g->h_ctl->rounds < capacity ? g->h_ctl->rounds : capacity;
+    int2 *h = (int2 *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int2));
+    if (!h) {
+      rc = fail(MF_ERR_OOM, "host allocation");
+    } else {
+      e = cudaMemcpy(h, tr, (size_t)nr * sizeof(int2), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) rc = cuda_fail(e, "trace copy");
+      for (long long k = 0; k < nr && rc == MF_OK; k++) {
+        live[k] = h[k].x;
+        relabel_before[k] = h[k].y;
+      }
+      free(h);
+    }
+  }
+  if (rounds && rc == MF_OK) *rounds = g->h_ctl->rounds;
+  if (tr) cudaFree(tr);
+  return rc;
+}
+
 int mf_get_stats(const mf_graph *g, mf_stats *out) {
   clear_error();
   if (!g || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
@@ -521,9 +557,9 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }
   if (label) {
-    int2 *tmp = (int2 *)malloc(n * sizeof(int2));
+    int4 *tmp = (int4 *)malloc(n * sizeof(int4));
     if (!tmp) return fail(MF_ERR_OOM, "host allocation");
-    e = cudaMemcpyAsync(tmp, g->vl, n * sizeof(int2), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaMemcpyAsync(tmp, g->vs, n * sizeof(int4), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     for (size_t v = 0; v < n && e == cudaSuccess; v++) label[v] = tmp[v].x > g->n ? g->n : tmp[v].x;
     free(tmp);

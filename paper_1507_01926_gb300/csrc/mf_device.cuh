@@ -17,24 +17,31 @@ enum Mode : int {
 
 // Control block in device memory, zeroed before every launch.
 struct Ctl {
-  unsigned bar_count;  // grid barrier arrivals
-  unsigned bar_gen;    // grid barrier generation
+  unsigned long long bar;  // grid barrier arrivals (monotone)
   int err;             // 0 or an MF_ERR_* code
   int err_where;       // which wait or check failed
-  int cnt[3];          // list sizes of generations g % 3
-  int live[3];         // live (non-dead) entries of generations g % 3
-  long long work[2];   // per-round relabel work, by round parity
+  int cnt[4];          // list sizes of generations g % 4
+  long long work[3];   // per-round relabel work, by round % 3
+  int gr_req[2];       // time-based relabel request, by round parity
   long long value;     // flow value (excess of the sink after phase 1)
   long long leftover;  // vertices still holding excess after phase 2
   // statistics
   long long rounds, rounds_phase1, grs, levels;
   long long scans_dis, scans_bfs, pushes, relabels;
   long long visits_dis, visits_bfs;
+  unsigned long long t_gr, t_dis;            // ns in global relabels / rounds (CTA 0's view)
+  long long rounds_by_size[4];               // rounds with <1K, <16K, <256K, more list entries
   unsigned long long t_start, t_preflow, t_end;  // %globaltimer, ns
   int stopped_round;   // MODE_ROUNDS: rounds run
 };
 
 // Device view of one (possibly multi-instance) graph.
+//
+// Vertex state vs[v] = {label slot 0, label slot 1, active stamp slot 0,
+// active stamp slot 1} (one 16-byte gather per arc). Round r reads the label
+// of every vertex from slot r & 1 and a discharged vertex writes d' into slot
+// (r + 1) & 1; a vertex is in the working set of round r iff its stamp in slot
+// r & 1 equals r. Slot 0 holds the labels during a BFS and at phase ends.
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
@@ -45,12 +52,10 @@ struct Dev {
   const int *__restrict__ rev;   // m
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
-  int2 *vl;          // n: {label d, round stamp of active-set membership}
-  int *dn;           // n: d' (label after this round's discharge)
+  int4 *vs;          // n: vertex state (above)
   long long *e;      // n: excess
-  long long *added;  // n: excess received this round by a vertex being discharged
-  int *disc;         // n: round stamp of the last test-and-set discovery
-  int *list[2];      // vertex lists, generation g uses list[g & 1]
+  long long *added;  // n: excess received while the vertex is in the working set
+  int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance
   int ninst;
@@ -60,12 +65,16 @@ struct Dev {
   int bin_warp;
   int beta;
   long long gr_threshold;  // global relabel when work since the last one exceeds this
+  double gr_time_ratio;    // also when time since the last one exceeds this times its duration (0 = off)
   long long max_rounds;
   unsigned long long timeout_ns;
   int mode;
   long long stop_rounds;
   int final_gr;
   int cut_only;
+  // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
+  int2 *trace;
+  long long trace_cap;
   // outputs (device pointers, each nullable)
   long long *out_value;   // per instance
   int *out_flow;          // m

@@ -19,11 +19,10 @@ struct mf_graph {
   int grid = 0, block = 0;
   // device state
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
-  int2 *rr = nullptr, *vl = nullptr;
-  int *dn = nullptr;
+  int2 *rr = nullptr;
+  int4 *vs = nullptr;
   long long *e = nullptr, *added = nullptr;
-  int *disc = nullptr;
-  int *list[2] = {nullptr, nullptr};
+  int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
   int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)
   mf::Ctl *ctl = nullptr;

@@ -3,31 +3,34 @@
 // persistent cooperative kernel for sm_103a.
 //
 // One launch runs a whole solve: initialisation and source saturation,
-// phase 1 (rounds of discharge + apply, a BFS global relabel whenever the
-// relabel work since the last one exceeds the threshold), phase 2 (the same
-// rounds toward s return the excess that cannot reach t), the cut BFS from s
-// and the outputs. Phases are separated by a grid barrier whose waits are
-// bounded in time (MF_ERR_TIMEOUT instead of a hang).
+// phase 1 (rounds of discharge, a BFS global relabel whenever the relabel work
+// since the last one exceeds the threshold), phase 2 (the same rounds toward
+// s return the excess that cannot reach t), the cut BFS from s and the
+// outputs. Phases are separated by a grid barrier whose waits are bounded in
+// time (MF_ERR_TIMEOUT instead of a hang). A round needs one barrier: the
+// label a vertex computes in round r goes to the other parity slot, and the
+// merge steps of Algorithm 1 (d := d', e += addedExcess) for round r run
+// during round r + 1, where they touch nothing that round reads.
 //
 // Data model (mf_device.cuh): CSR of paired slots with an inline copy of the
 // reverse residual (int2 rr[a] = {res[a], res[rev[a]]}, the "each edge also
 // stores the residual capacity of its reverse edge" layout of Section 4.2),
-// per-vertex int2 vl[v] = {label, round stamp of active-set membership},
-// int64 excess. Vertex lists are plain arrays filled by warp-aggregated
-// atomics; a list is consumed in tiles of blockDim entries that are binned in
-// shared memory by degree (thread / warp / CTA per vertex).
+// per-vertex int4 vs[v] = {label slots, active-round stamps}, int64 excess.
+// Vertex lists are plain arrays filled by warp-aggregated atomics; a list is
+// consumed in tiles of blockDim entries that are binned in shared memory by
+// degree (thread / warp / CTA per vertex).
 //
 // Readings of the listing that the kernel follows (Algorithm 1):
 //  * the activity test of a neighbour w ("if e(w)") is membership of w in the
-//    current working set, kept as vl[w].y == round;
+//    current working set, kept as a round stamp;
 //  * pushes use the local excess of the discharging vertex;
-//  * excess received by a vertex that is itself being discharged goes to its
-//    addedExcess (atomic), excess received by any other vertex is added to its
-//    excess directly (atomic; nobody reads it during the round);
+//  * excess received by a vertex of the working set goes to its addedExcess
+//    (atomic), excess received by any other vertex is added to its excess
+//    directly (atomic; nobody reads it during the round);
 //  * the next working set holds every vertex that received excess (not the
-//    sink) plus every discharged vertex left with excess and d' < n, minus
-//    those whose label reached n; excess pushed into the sink accumulates into
-//    e(sink), which is the flow value;
+//    sink) plus every discharged vertex left with excess and d' < n; a vertex
+//    whose label reached n is skipped when its turn comes; excess pushed into
+//    the sink accumulates into e(sink), which is the flow value;
 //  * arcs of one vertex are scanned in CSR order; a warp or CTA reproduces
 //    that order with an exclusive prefix sum of the pushable residuals;
 //  * the source keeps label n + 1 internally (equivalent to n: no label
@@ -49,7 +52,7 @@ namespace cg = cooperative_groups;
 namespace mf {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int KT = 8;         // largest degree handled by one thread (register-cached arcs)
+constexpr int KT = 8;           // largest degree handled by one thread (register-cached arcs)
 constexpr int MAX_BLOCK = 512;  // largest CTA
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
 
@@ -61,25 +64,38 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigned long long x) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
 }
 
 __device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
 
-__device__ __forceinline__ int *label_ptr(const Dev &D, int v) { return reinterpret_cast<int *>(&D.vl[v]); }
-__device__ __forceinline__ int *stamp_ptr(const Dev &D, int v) { return reinterpret_cast<int *>(&D.vl[v]) + 1; }
+// label slot p / active stamp slot p of v
+__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return reinterpret_cast<int *>(&D.vs[v]) + p; }
+__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) {
+  return reinterpret_cast<int *>(&D.vs[v]) + 2 + p;
+}
+__device__ __forceinline__ int lab_of(const int4 &x, int p) { return p ? x.y : x.x; }
+__device__ __forceinline__ int act_of(const int4 &x, int p) { return p ? x.w : x.z; }
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
 __device__ __forceinline__ void set_err(const Dev &D, int code, int where) {
   if (atomicCAS(&D.ctl->err, 0, code) == 0) atomicExch(&D.ctl->err_where, where);
+}
+
+__device__ __forceinline__ long long take_added(const Dev &D, int v) {
+  return (long long)atomicExch(reinterpret_cast<unsigned long long *>(&D.added[v]), 0ULL);
+}
+
+__device__ __forceinline__ void atomic_add64(long long *p, long long x) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)x);
 }
 
 // Win rule of Section 3.1 for two active neighbours, on the labels at the
@@ -99,24 +115,24 @@ __device__ __forceinline__ void push_res(const Dev &D, int a, int ra, int delta)
   atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[ra]), d64 - (d64 << 32));
 }
 
-// Appends one value per calling thread to list/cnt with one atomic per
-// converged group of lanes. Lists hold at most n entries (every list holds
-// distinct vertices); an overflow would be a solver bug and is reported as
-// MF_ERR_INTERNAL instead of being written.
-__device__ __forceinline__ void append(const Dev &D, int *list, int *cnt, int val) {
+__device__ __forceinline__ int list_count(const Dev &D, int gen) { return min(__ldcg(&D.ctl->cnt[gen & 3]), D.n); }
+__device__ __forceinline__ int *list_of(const Dev &D, int gen) { return D.list[gen % 3]; }
+
+// Appends one value per calling thread to the list of generation gen with one
+// atomic per converged group of lanes. Lists hold at most n entries (every
+// list holds distinct vertices); an overflow would be a solver bug and is
+// reported as MF_ERR_INTERNAL instead of being written.
+__device__ __forceinline__ void append(const Dev &D, int gen, int val) {
   cg::coalesced_group g = cg::coalesced_threads();
   int base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(cnt, (int)g.size());
+  if (g.thread_rank() == 0) base = atomicAdd(&D.ctl->cnt[gen & 3], (int)g.size());
   base = g.shfl(base, 0);
   const int idx = base + (int)g.thread_rank();
   if (idx < D.n)
-    list[idx] = val;
+    list_of(D, gen)[idx] = val;
   else
     set_err(D, MF_ERR_INTERNAL, 11);
 }
-
-// Entries of list generation gen (never more than n).
-__device__ __forceinline__ int list_count(const Dev &D, int gen) { return min(__ldcg(&D.ctl->cnt[gen % 3]), D.n); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
@@ -141,12 +157,11 @@ __device__ __forceinline__ long long warp_incl_scan(long long x, int lane) {
 }
 
 struct Shared {
-  unsigned gen;
+  unsigned long long bars;  // grid barriers passed by this CTA
   int pick;
   int flag;
   int imin[MAX_WARPS];
   long long lsum[MAX_WARPS];
-  long long bval;
 };
 
 // Block-wide sum of a 64-bit value (all threads call; result valid in all).
@@ -162,31 +177,29 @@ __device__ long long block_sum(long long x, Shared &sh) {
   return t;
 }
 
-// Grid barrier. Every wait is bounded by D.timeout_ns; on expiry the error
-// word is set and all blocks leave at their next barrier.
+// Grid barrier on a monotone 64-bit arrival counter: CTA k's b-th arrival is
+// complete when the counter reaches b * gridDim.x. Every wait is bounded by
+// D.timeout_ns; on expiry the error word is set and all CTAs leave at their
+// next barrier.
 __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    Ctl *c = D.ctl;
-    unsigned g = sh.gen;
+    unsigned long long *c = reinterpret_cast<unsigned long long *>(&D.ctl->bar);
+    const unsigned long long target = (sh.bars + 1) * (unsigned long long)gridDim.x;
     __threadfence();
-    unsigned prev = atomicAdd(&c->bar_count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(&c->bar_count, 0u);
-      __threadfence();
-      st_release(&c->bar_gen, g + 1);
-    } else {
-      unsigned long long t0 = gtimer();
+    red_release_add64(c, 1ULL);
+    if (ld_acquire64(c) < target) {
+      const unsigned long long t0 = gtimer();
       unsigned spins = 0;
-      while (ld_acquire(&c->bar_gen) == g) {
+      while (ld_acquire64(c) < target) {
         if ((++spins & 31u) == 0 && gtimer() - t0 > D.timeout_ns) {
           set_err(D, MF_ERR_TIMEOUT, where);
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
-    sh.gen = g + 1;
+    sh.bars++;
     __threadfence();
   }
   __syncthreads();
@@ -199,8 +212,9 @@ struct TStat {
 
 // ------------------------------------------------------------------ discharge
 //
-// Algorithm 1, inner loop, for one vertex v of the working set: with the local
-// excess ex and d' = d(v), repeat passes over the residual arcs in order:
+// Algorithm 1, inner loop, for one vertex v of the working set of round r
+// (labels read from slot p = r & 1): with the local excess ex and d' = d(v),
+// repeat passes over the residual arcs in order:
 //   admissible  <=> d'(v) = d(w) + 1 (old label of w);
 //   w active and v loses the win rule and the arc is admissible => skip the
 //     arc and end the discharge after this pass;
@@ -209,24 +223,25 @@ struct TStat {
 // After a pass: stop when ex = 0 or an arc was skipped; else d' := candidate
 // minimum (starting at n), work += deg + beta, stop when d' = n.
 
-// Excess delta reaches w: the sink (label 0) accumulates it in a register of
-// the caller, a vertex being discharged this round gets it in addedExcess,
-// any other vertex directly in its excess. Returns true when w must join the
+struct RoundCtx {
+  int r;     // round stamp
+  int p;     // r & 1
+  int next;  // list generation receiving the next working set
+};
+
+// Excess delta reaches w (not the sink). Returns true when w must join the
 // next working set through this call (first discovery this round).
-__device__ __forceinline__ bool deliver(const Dev &D, int w, int dw, bool w_active, long long delta, int r) {
-  if (w_active)
-    atomicAdd(reinterpret_cast<unsigned long long *>(&D.added[w]), (unsigned long long)delta);
-  else
-    atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[w]), (unsigned long long)delta);
-  return atomicExch(&D.disc[w], r) != r;
+__device__ __forceinline__ bool deliver(const Dev &D, const RoundCtx &R, int w, bool w_active, long long delta) {
+  atomic_add64(w_active ? &D.added[w] : &D.e[w], delta);
+  return atomicExch(act_ptr(D, w, R.p ^ 1), R.r + 1) != R.r + 1;
 }
 
-__device__ __forceinline__ void finish_vertex(const Dev &D, int v, int dp, long long ex, int cap_v, int r,
-                                              int *next, int *next_cnt) {
-  D.dn[v] = dp;
+__device__ __forceinline__ void finish_vertex(const Dev &D, const RoundCtx &R, int v, int dp, long long ex,
+                                              int cap_v) {
+  *lab_ptr(D, v, R.p ^ 1) = dp;
   D.e[v] = ex;
   if (ex > 0 && dp < cap_v) {
-    if (atomicExch(&D.disc[v], r) != r) append(D, next, next_cnt, v);
+    if (atomicExch(act_ptr(D, v, R.p ^ 1), R.r + 1) != R.r + 1) append(D, R.next, v);
   }
 }
 
@@ -237,12 +252,11 @@ __device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_
   cg::coalesced_group g = cg::coalesced_threads();
   cg::coalesced_group part = cg::labeled_partition(g, sink);
   const long long sum = cg::reduce(part, to_sink, cg::plus<long long>());
-  if (part.thread_rank() == 0)
-    atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[sink]), (unsigned long long)sum);
+  if (part.thread_rank() == 0) atomic_add64(&D.e[sink], sum);
 }
 
 // One thread, deg <= KT: arcs cached in registers for all passes.
-__device__ void discharge_thread(const Dev &D, int v, int beg, int deg, int r, int *next, int *next_cnt,
+__device__ void discharge_thread(const Dev &D, const RoundCtx &R, int v, int beg, int deg, int dv, int cap_v,
                                  TStat &st, long long &work) {
   int wv[KT], rs[KT], dw[KT];
   unsigned act = 0;
@@ -259,14 +273,11 @@ __device__ void discharge_thread(const Dev &D, int v, int beg, int deg, int r, i
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (rs[i] > 0) {
-      const int2 x = __ldcg(&D.vl[wv[i]]);
-      dw[i] = x.x;
-      if (x.y == r) act |= 1u << i;
+      const int4 x = __ldcg(&D.vs[wv[i]]);
+      dw[i] = lab_of(x, R.p);
+      if (act_of(x, R.p) == R.r) act |= 1u << i;
     }
-  const int2 me = __ldcg(&D.vl[v]);
-  const int dv = me.x;
-  const int cap_v = cap_of(D, v);
-  long long ex = __ldcg(&D.e[v]);
+  long long ex = __ldcg(&D.e[v]) + take_added(D, v);
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
@@ -291,7 +302,7 @@ __device__ void discharge_thread(const Dev &D, int v, int beg, int deg, int r, i
             if (dw[i] == 0) {
               to_sink += delta;
               sink = wv[i];
-            } else if (deliver(D, wv[i], dw[i], (act >> i) & 1u, delta, r)) {
+            } else if (deliver(D, R, wv[i], (act >> i) & 1u, delta)) {
               found |= 1u << i;
             }
           }
@@ -305,21 +316,22 @@ __device__ void discharge_thread(const Dev &D, int v, int beg, int deg, int r, i
     work += deg + D.beta;
     if (dp >= cap_v) break;
   }
-  finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+  finish_vertex(D, R, v, dp, ex, cap_v);
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if ((found >> i) & 1u) append(D, next, next_cnt, wv[i]);
+    if ((found >> i) & 1u) append(D, R.next, wv[i]);
   flush_sink(D, sink, to_sink);
 }
 
 // One warp (all 32 lanes call), arcs in chunks of 32.
-__device__ void discharge_warp(const Dev &D, int v, int r, int *next, int *next_cnt, TStat &st, long long &work) {
+__device__ void discharge_warp(const Dev &D, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
+                               long long &work) {
   const int lane = threadIdx.x & 31;
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
-  const int dv = __ldcg(&D.vl[v]).x;
-  const int cap_v = cap_of(D, v);
-  long long ex = __ldcg(&D.e[v]);
+  long long ex = 0;
+  if (lane == 0) ex = __ldcg(&D.e[v]) + take_added(D, v);
+  ex = __shfl_sync(FULL, ex, 0);
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
@@ -334,9 +346,9 @@ __device__ void discharge_warp(const Dev &D, int v, int r, int *next, int *next_
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          int2 x = __ldcg(&D.vl[w]);
-          dw = x.x;
-          wact = (x.y == r);
+          const int4 x = __ldcg(&D.vs[w]);
+          dw = lab_of(x, R.p);
+          wact = act_of(x, R.p) == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -359,10 +371,10 @@ __device__ void discharge_warp(const Dev &D, int v, int r, int *next, int *next_
           to_sink += delta;
           sink = w;
         } else {
-          found = deliver(D, w, dw, wact, delta, r);
+          found = deliver(D, R, w, wact, delta);
         }
       }
-      if (found) append(D, next, next_cnt, w);
+      if (found) append(D, R.next, w);
       if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
       skipped |= (__ballot_sync(FULL, skip) != 0);
       ex = total >= ex ? 0 : ex - total;
@@ -376,21 +388,22 @@ __device__ void discharge_warp(const Dev &D, int v, int r, int *next, int *next_
     }
     if (dp >= cap_v) break;
   }
-  if (lane == 0) finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+  if (lane == 0) finish_vertex(D, R, v, dp, ex, cap_v);
   __syncwarp();
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncwarp();
 }
 
 // One CTA (all threads call), arcs in chunks of blockDim.
-__device__ void discharge_block(const Dev &D, int v, int r, int *next, int *next_cnt, TStat &st, long long &work,
-                                Shared &sh) {
+__device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
+                                long long &work, Shared &sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
-  const int dv = __ldcg(&D.vl[v]).x;
-  const int cap_v = cap_of(D, v);
-  long long ex = __ldcg(&D.e[v]);
+  __syncthreads();
+  if (threadIdx.x == 0) sh.lsum[0] = __ldcg(&D.e[v]) + take_added(D, v);
+  __syncthreads();
+  long long ex = sh.lsum[0];
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
@@ -405,9 +418,9 @@ __device__ void discharge_block(const Dev &D, int v, int r, int *next, int *next
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          int2 x = __ldcg(&D.vl[w]);
-          dw = x.x;
-          wact = (x.y == r);
+          const int4 x = __ldcg(&D.vs[w]);
+          dw = lab_of(x, R.p);
+          wact = act_of(x, R.p) == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -439,10 +452,10 @@ __device__ void discharge_block(const Dev &D, int v, int r, int *next, int *next
           to_sink += delta;
           sink = w;
         } else {
-          found = deliver(D, w, dw, wact, delta, r);
+          found = deliver(D, R, w, wact, delta);
         }
       }
-      if (found) append(D, next, next_cnt, w);
+      if (found) append(D, R.next, w);
       if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
       if (skip) sh.flag = 1;
       __syncthreads();
@@ -464,114 +477,115 @@ __device__ void discharge_block(const Dev &D, int v, int r, int *next, int *next
     }
     if (dp >= cap_v) break;
   }
-  if (threadIdx.x == 0) finish_vertex(D, v, dp, ex, cap_v, r, next, next_cnt);
+  if (threadIdx.x == 0) finish_vertex(D, R, v, dp, ex, cap_v);
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncthreads();
 }
 
-// Discharge every vertex of list generation `gen`; discoveries go to gen + 1.
-__device__ void discharge_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd, TStat &st) {
-  const int *W = D.list[gen & 1];
-  int *next = D.list[(gen + 1) & 1];
-  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
-  const int count = list_count(D, gen);
+// A vertex in the working set of round r whose label has reached the cap (it
+// was discovered while it relabeled to n): carry its label into the next slot
+// and fold its addedExcess into its excess.
+__device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int v, int dv) {
+  *lab_ptr(D, v, R.p ^ 1) = dv;
+  const long long ad = take_added(D, v);
+  if (ad) D.e[v] = __ldcg(&D.e[v]) + ad;
+}
+
+// One round: (1) merge step of the previous round for its vertices that are
+// not in this working set (label carried into the next slot, addedExcess
+// folded into the excess); (2) discharge every vertex of this working set
+// (list generation gen), discoveries to generation gen + 1.
+__device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, long long rnd, TStat &st) {
+  const RoundCtx R{r, r & 1, gen + 1};
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    D.ctl->cnt[(gen + 2) % 3] = 0;
-    D.ctl->live[(gen + 2) % 3] = 0;
+    D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->work[(rnd + 1) % 3] = 0;
   }
+  if (prev_valid) {
+    const int *P = list_of(D, gen - 1);
+    const int cp = list_count(D, gen - 1);
+    for (int i = tid; i < cp; i += nthr) {
+      const int u = __ldcg(&P[i]);
+      if (__ldcg(act_ptr(D, u, R.p)) == r) continue;  // in this working set: handled below
+      *lab_ptr(D, u, R.p ^ 1) = __ldcg(lab_ptr(D, u, R.p));
+      const long long ad = take_added(D, u);
+      if (ad) atomic_add64(&D.e[u], ad);  // excess of a non-member may receive pushes now
+    }
+  }
+  const int *W = list_of(D, gen);
+  const int count = list_count(D, gen);
   const int lane = threadIdx.x & 31;
   long long work = 0;
   for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
     const int idx = base + threadIdx.x;
-    int v = idx < count ? __ldcg(&W[idx]) : -1;
-    int beg = 0, deg = 0, cls = 0;
+    const int v = idx < count ? __ldcg(&W[idx]) : -1;
+    int beg = 0, deg = 0, cls = 0, dv = 0, cap_v = 0;
     if (v >= 0) {
-      beg = __ldg(&D.row[v]);
-      deg = __ldg(&D.row[v + 1]) - beg;
-      cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
-      st.visits_dis++;
+      dv = __ldcg(lab_ptr(D, v, R.p));
+      cap_v = cap_of(D, v);
+      if (dv >= cap_v) {
+        retire_dead(D, R, v, dv);
+      } else {
+        beg = __ldg(&D.row[v]);
+        deg = __ldg(&D.row[v + 1]) - beg;
+        cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
+        st.visits_dis++;
+      }
     }
     for (;;) {  // CTA per vertex
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
-      if (cls == 3) sh.pick = v;
+      if (cls == 3) sh.pick = threadIdx.x;
       __syncthreads();
-      const int pv = sh.pick;
-      if (pv < 0) break;
-      if (v == pv) cls = 0;
-      discharge_block(D, pv, r, next, next_cnt, st, work, sh);
+      const int pt = sh.pick;
+      if (pt < 0) break;
+      if (threadIdx.x == pt) {
+        cls = 0;
+        sh.imin[0] = v;
+        sh.imin[1] = dv;
+        sh.imin[2] = cap_v;
+      }
+      __syncthreads();
+      const int bv = sh.imin[0], bdv = sh.imin[1], bcap = sh.imin[2];
+      discharge_block(D, R, bv, bdv, bcap, st, work, sh);
     }
     for (;;) {  // warp per vertex
       const unsigned mm = __ballot_sync(FULL, cls == 2);
       if (!mm) break;
       const int leader = __ffs(mm) - 1;
       const int pv = __shfl_sync(FULL, v, leader);
+      const int pdv = __shfl_sync(FULL, dv, leader);
+      const int pcap = __shfl_sync(FULL, cap_v, leader);
       if (lane == leader) cls = 0;
-      discharge_warp(D, pv, r, next, next_cnt, st, work);
+      discharge_warp(D, R, pv, pdv, pcap, st, work);
     }
-    if (cls == 1) discharge_thread(D, v, beg, deg, r, next, next_cnt, st, work);
+    if (cls == 1) discharge_thread(D, R, v, beg, deg, dv, cap_v, st, work);
     __syncwarp();
   }
   const long long wsum = block_sum(work, sh);
-  if (threadIdx.x == 0 && wsum) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->work[rnd & 1]),
-                                          (unsigned long long)wsum);
-}
-
-// Algorithm 1 after the discharge: old working set takes d := d' and its
-// addedExcess; the new list keeps the vertices whose label (d' if they were
-// discharged) is below the cap and stamps them active for round r + 1.
-__device__ void apply_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  const int *W = D.list[gen & 1];
-  int *N = D.list[(gen + 1) & 1];
-  const int cw = list_count(D, gen);
-  const int cn = list_count(D, gen + 1);
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->work[(rnd + 1) & 1] = 0;
-  for (int i = tid; i < cw; i += nthr) {
-    const int v = __ldcg(&W[i]);
-    if (v < 0) continue;
-    *label_ptr(D, v) = __ldcg(&D.dn[v]);
-    const long long ad = __ldcg(&D.added[v]);
-    if (ad) {
-      D.e[v] = __ldcg(&D.e[v]) + ad;
-      D.added[v] = 0;
-    }
-  }
-  int live = 0;
-  for (int i = tid; i < cn; i += nthr) {
-    const int u = __ldcg(&N[i]);
-    const int2 x = __ldcg(&D.vl[u]);
-    const int de = (x.y == r) ? __ldcg(&D.dn[u]) : x.x;
-    if (de < cap_of(D, u)) {
-      *stamp_ptr(D, u) = r + 1;
-      live++;
-    } else {
-      N[i] = -1;
-    }
-  }
-  const long long ls = block_sum(live, sh);
-  if (threadIdx.x == 0 && ls) atomicAdd(&D.ctl->live[(gen + 1) % 3], (int)ls);
+  if (threadIdx.x == 0 && wsum) atomic_add64(&D.ctl->work[rnd % 3], wsum);
 }
 
 // ------------------------------------------------------------------ BFS
 //
-// Level-synchronous BFS (Algorithm 2). A frontier vertex v at level k
-// discovers w through slot a = (v -> w) when the tested residual is positive
-// (reverse BFS for the global relabel: res[rev[a]] = c_f(w, v); forward BFS for
-// the cut: res[a] = c_f(v, w)) and CAS(label(w): UNV -> k + 1) succeeds.
+// Level-synchronous BFS (Algorithm 2) on label slot 0. A frontier vertex v at
+// level k discovers w through slot a = (v -> w) when the tested residual is
+// positive (reverse BFS for the global relabel: res[rev[a]] = c_f(w, v);
+// forward BFS for the cut: res[a] = c_f(v, w)) and CAS(label(w): UNV -> k + 1)
+// succeeds.
 
-__device__ __forceinline__ void bfs_arc(const Dev &D, int a, int lvl, bool reverse, int *next, int *next_cnt) {
+__device__ __forceinline__ void bfs_arc(const Dev &D, int a, int lvl, bool reverse, int next) {
   const int w = __ldg(&D.head[a]);
   const int2 x = __ldcg(&D.rr[a]);
   const int cf = reverse ? x.y : x.x;
-  if (cf > 0 && __ldcg(label_ptr(D, w)) == UNV) {
-    if (atomicCAS(label_ptr(D, w), UNV, lvl + 1) == UNV) append(D, next, next_cnt, w);
+  if (cf > 0 && __ldcg(lab_ptr(D, w, 0)) == UNV) {
+    if (atomicCAS(lab_ptr(D, w, 0), UNV, lvl + 1) == UNV) append(D, next, w);
   }
 }
 
 // One thread, deg <= KT, loads issued together.
-__device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int lvl, bool reverse, int *next,
-                                           int *next_cnt) {
+__device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int lvl, bool reverse, int next) {
   int w[KT], cf[KT], lab[KT];
 #pragma unroll
   for (int i = 0; i < KT; i++) {
@@ -584,22 +598,17 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int l
     }
   }
 #pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(label_ptr(D, w[i])) : 0;
+  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(lab_ptr(D, w[i], 0)) : 0;
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(label_ptr(D, w[i]), UNV, lvl + 1) == UNV)
-      append(D, next, next_cnt, w[i]);
+    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) == UNV) append(D, next, w[i]);
 }
 
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
-  const int *F = D.list[gen & 1];
-  int *next = D.list[(gen + 1) & 1];
-  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  const int *F = list_of(D, gen);
+  const int next = gen + 1;
   const int count = list_count(D, gen);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    D.ctl->cnt[(gen + 2) % 3] = 0;
-    D.ctl->live[(gen + 2) % 3] = 0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
   const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
     const int idx = base + threadIdx.x;
@@ -621,7 +630,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       if (pv < 0) break;
       if (v == pv) cls = 0;
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, a, lvl, reverse, next, next_cnt);
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, a, lvl, reverse, next);
       __syncthreads();
     }
     for (;;) {
@@ -631,56 +640,47 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       const int pv = __shfl_sync(FULL, v, leader);
       if (lane == leader) cls = 0;
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + lane; a < e; a += 32) bfs_arc(D, a, lvl, reverse, next, next_cnt);
+      for (int a = b + lane; a < e; a += 32) bfs_arc(D, a, lvl, reverse, next);
       __syncwarp();
     }
-    if (cls == 1) bfs_thread(D, beg, deg, lvl, reverse, next, next_cnt);
+    if (cls == 1) bfs_thread(D, beg, deg, lvl, reverse, next);
     __syncwarp();
   }
 }
 
-// BFS from `seeds` (label 0). `blockers` get UNV + 1 and are never reached.
-// With `excess_seeds`, every vertex holding excess whose label lies in
-// [1, cap] is a seed as well (cut from the maximum preflow). Returns false on
-// error. On return the last list generation is empty.
+// BFS from `seeds` (label 0) on label slot 0. `blockers` get UNV + 1 and are
+// never reached. With `excess_seeds`, every vertex holding excess whose label
+// lies in [1, cap] is a seed as well (cut from the maximum preflow). Returns
+// false on error. On return the last list generation (gen) is empty.
 __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *blockers, int nterm, bool reverse,
                     bool excess_seeds, int &gen, TStat &st, int where) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  int *next = D.list[(gen + 1) & 1];
-  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  const int next = gen + 1;
   // phase A: every label to UNV (excess-holding non-terminals become seeds)
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    D.ctl->cnt[(gen + 2) % 3] = 0;
-    D.ctl->live[(gen + 2) % 3] = 0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
   for (int v = tid; v < D.n; v += nthr) {
     int x = UNV;
     if (excess_seeds) {
-      const int d = __ldcg(label_ptr(D, v));
+      const int d = __ldcg(lab_ptr(D, v, 0));
       if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) > 0) {
         x = 0;
-        append(D, next, next_cnt, v);
+        append(D, next, v);
       }
     }
-    *label_ptr(D, v) = x;
+    *lab_ptr(D, v, 0) = x;
   }
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
-    *label_ptr(D, seeds[i]) = 0;
-    if (blockers) *label_ptr(D, blockers[i]) = UNV + 1;
+    *lab_ptr(D, seeds[i], 0) = 0;
+    if (blockers) *lab_ptr(D, blockers[i], 0) = UNV + 1;
   }
-  if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < nterm; i += blockDim.x) {
-      int x = seeds[i];
-      append(D, next, next_cnt, x);
-    }
-  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nterm; i += blockDim.x) append(D, next, seeds[i]);
   if (!grid_sync(D, sh, where)) return false;
   gen++;
-  // excess seeds may repeat a terminal seed; a repeat only rescans its arcs
   for (int lvl = 0;; lvl++) {
-    if (__ldcg(&D.ctl->cnt[gen % 3]) == 0) break;
+    if (list_count(D, gen) == 0) break;
     bfs_level(D, sh, gen, lvl, reverse, st);
     if (!grid_sync(D, sh, where)) return false;
     gen++;
@@ -691,36 +691,55 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
 
 // Global relabel (Algorithm 2 from the sinks, never entering the sources),
 // then the working set is rebuilt for round r: labels left at UNV become the
-// cap n, sources n + 1, and every vertex with excess and 0 < d < n is
-// stamped active. Result: list generation gen.
+// cap n, sources n + 1, both label slots get the result, addedExcess is folded
+// into the excess, and every vertex with excess and 0 < d < n is stamped
+// active. Result: list generation gen.
 __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const int *sources, int r, int &gen,
                                TStat &st) {
   if (!bfs(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2)) return false;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  int *next = D.list[(gen + 1) & 1];
-  int *next_cnt = &D.ctl->cnt[(gen + 1) % 3];
+  const int next = gen + 1;
+  const int p = r & 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    D.ctl->cnt[(gen + 2) % 3] = 0;
-    D.ctl->live[(gen + 2) % 3] = 0;
+    D.ctl->cnt[(gen + 2) & 3] = 0;
     D.ctl->grs++;
   }
-  int live = 0;
   for (int v = tid; v < D.n; v += nthr) {
-    const int x = __ldcg(label_ptr(D, v));
+    const int x = __ldcg(lab_ptr(D, v, 0));
     const int c = cap_of(D, v);
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
-    if (d != x) *label_ptr(D, v) = d;
-    if (d > 0 && d < c && __ldcg(&D.e[v]) > 0) {
-      *stamp_ptr(D, v) = r;
-      append(D, next, next_cnt, v);
-      live++;
+    *reinterpret_cast<int2 *>(&D.vs[v]) = make_int2(d, d);
+    long long ev = __ldcg(&D.e[v]);
+    const long long ad = __ldcg(&D.added[v]);
+    if (ad) {
+      ev += ad;
+      D.e[v] = ev;
+      D.added[v] = 0;
+    }
+    if (d > 0 && d < c && ev > 0) {
+      *act_ptr(D, v, p) = r;
+      append(D, next, v);
     }
   }
-  const long long ls = block_sum(live, sh);
-  if (threadIdx.x == 0 && ls) atomicAdd(&D.ctl->live[(gen + 1) % 3], (int)ls);
   if (!grid_sync(D, sh, 3)) return false;
   gen++;
   return true;
+}
+
+// Ends a MODE_ROUNDS run between rounds: every vertex gets its current label
+// (slot p) in both slots and its addedExcess folded into its excess.
+__device__ bool settle(const Dev &D, Shared &sh, int p) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  for (int v = tid; v < D.n; v += nthr) {
+    const int d = __ldcg(lab_ptr(D, v, p));
+    *reinterpret_cast<int2 *>(&D.vs[v]) = make_int2(d, d);
+    const long long ad = __ldcg(&D.added[v]);
+    if (ad) {
+      D.e[v] = __ldcg(&D.e[v]) + ad;
+      D.added[v] = 0;
+    }
+  }
+  return grid_sync(D, sh, 12);
 }
 
 // Rounds of Algorithm 1 toward `sinks` until no vertex is active right after a
@@ -728,17 +747,27 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
 __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int *sources, int &r, int &gen,
                           long long &rnd, bool phase1, TStat &st) {
   long long since_gr = LLONG_MAX;
-  bool fresh = false;
+  bool fresh = false, time_req = false, prev_valid = false;
   long long rounds = 0;
+  unsigned long long last_gr_ns = 0, last_gr_end = 0;  // meaningful in CTA 0 thread 0 only
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   for (;;) {
-    if (since_gr > D.gr_threshold) {
+    if (since_gr > D.gr_threshold || time_req) {
       r++;  // fresh stamp: marks of the discarded working set are stale
+      const unsigned long long t0 = timer ? gtimer() : 0;
       if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+      if (timer) {
+        last_gr_end = gtimer();
+        last_gr_ns = last_gr_end - t0;
+        D.ctl->t_gr += last_gr_ns;
+      }
       since_gr = 0;
       fresh = true;
+      time_req = false;
+      prev_valid = false;
     }
-    const int live = __ldcg(&D.ctl->live[gen % 3]);
-    if (live == 0) {
+    const int count = list_count(D, gen);
+    if (count == 0) {
       if (fresh) break;
       since_gr = LLONG_MAX;
       continue;
@@ -748,26 +777,37 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       set_err(D, MF_ERR_ITER_LIMIT, 10);
       return false;
     }
+    unsigned long long t0 = 0;
+    if (timer) {
+      D.ctl->rounds_by_size[count < 1024 ? 0 : count < 16384 ? 1 : count < 262144 ? 2 : 3]++;
+      if (D.trace && rnd < D.trace_cap) D.trace[rnd] = make_int2(count, fresh ? 1 : 0);
+      t0 = gtimer();
+      D.ctl->gr_req[rnd & 1] =
+          D.gr_time_ratio > 0 && (double)(t0 - last_gr_end) > D.gr_time_ratio * (double)last_gr_ns;
+    }
     fresh = false;
-    discharge_phase(D, sh, r, gen, rnd, st);
+    round_phase(D, sh, r, gen, prev_valid, rnd, st);
     if (!grid_sync(D, sh, 4)) return false;
-    apply_phase(D, sh, r, gen, rnd);
-    if (!grid_sync(D, sh, 5)) return false;
-    since_gr += __ldcg(&D.ctl->work[rnd & 1]);
+    if (timer) D.ctl->t_dis += gtimer() - t0;
+    since_gr += __ldcg(&D.ctl->work[rnd % 3]);
+    time_req = __ldcg(&D.ctl->gr_req[rnd & 1]) != 0;
     r++;
     gen++;
     rnd++;
     rounds++;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    prev_valid = true;
+    if (timer) {
       D.ctl->rounds++;
       if (phase1) D.ctl->rounds_phase1++;
     }
   }
   if (D.mode == MODE_ROUNDS) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->stopped_round = (int)rounds;
+    if (timer) D.ctl->stopped_round = (int)rounds;
     if (D.final_gr) {
       r++;
       if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+    } else if (!fresh) {
+      if (!settle(D, sh, r & 1)) return false;
     }
   }
   return true;
@@ -777,7 +817,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
 
 __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
   __shared__ Shared sh;
-  if (threadIdx.x == 0) sh.gen = 0;
+  if (threadIdx.x == 0) sh.bars = 0;
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   TStat st;
@@ -787,11 +827,9 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
   // excess 0, no stamps.
   for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
   for (int v = tid; v < D.n; v += nthr) {
-    D.vl[v] = make_int2(0, -1);
-    D.dn[v] = 0;
+    D.vs[v] = make_int4(0, 0, -1, -1);
     D.e[v] = 0;
     D.added[v] = 0;
-    D.disc[v] = -1;
   }
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
@@ -807,7 +845,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
         const int cr = __ldg(&D.cap[ra]);
         D.rr[a] = make_int2(0, cr + c);
         D.rr[ra] = make_int2(cr + c, 0);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&D.e[w]), (unsigned long long)(long long)c);
+        atomic_add64(&D.e[w], c);
       }
     }
     ok = grid_sync(D, sh, 1);
@@ -831,12 +869,11 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
       if (ok) {
         long long left = 0;
         for (int v = tid; v < D.n; v += nthr) {
-          const int d = __ldcg(label_ptr(D, v));
+          const int d = __ldcg(lab_ptr(D, v, 0));
           if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) != 0) left++;
         }
         left = block_sum(left, sh);
-        if (threadIdx.x == 0 && left) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->leftover),
-                                                (unsigned long long)left);
+        if (threadIdx.x == 0 && left) atomic_add64(&D.ctl->leftover, left);
         ok = grid_sync(D, sh, 7);
         if (ok && __ldcg(&D.ctl->leftover) != 0) {
           set_err(D, MF_ERR_INTERNAL, 8);
@@ -853,7 +890,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
           unsigned bits = 0;
           for (int j = 0; j < 32; j++) {
             const int v = wd * 32 + j;
-            if (v < D.n && __ldcg(label_ptr(D, v)) != UNV) bits |= 1u << j;
+            if (v < D.n && __ldcg(lab_ptr(D, v, 0)) != UNV) bits |= 1u << j;
           }
           D.out_cut[wd] = bits;
         }
@@ -868,17 +905,17 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
   // statistics
   long long x;
   x = block_sum(st.scans_dis, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->scans_dis), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->scans_dis, x);
   x = block_sum(st.scans_bfs, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->scans_bfs), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->scans_bfs, x);
   x = block_sum(st.pushes, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->pushes), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->pushes, x);
   x = block_sum(st.relabels, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->relabels), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->relabels, x);
   x = block_sum(st.visits_dis, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->visits_dis), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->visits_dis, x);
   x = block_sum(st.visits_bfs, sh);
-  if (threadIdx.x == 0 && x) atomicAdd(reinterpret_cast<unsigned long long *>(&D.ctl->visits_bfs), (unsigned long long)x);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->visits_bfs, x);
   if (tid == 0) D.ctl->t_end = gtimer();
 }
 

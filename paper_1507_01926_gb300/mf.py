@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
     _fields_ = [("gr_freq", ctypes.c_double), ("gr_alpha", ctypes.c_int32), ("work_beta", ctypes.c_int32),
                 ("bin_thread", ctypes.c_int32), ("bin_warp", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int32),
-                ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32), ("gr_time_ratio", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -39,10 +39,14 @@ class Stats(ctypes.Structure):
                 ("bfs_levels", ctypes.c_int64), ("scans_discharge", ctypes.c_int64), ("scans_bfs", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("relabels", ctypes.c_int64), ("visits_discharge", ctypes.c_int64),
                 ("visits_bfs", ctypes.c_int64), ("solve_ms", ctypes.c_double),
-                ("preflow_ms", ctypes.c_double), ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("preflow_ms", ctypes.c_double), ("relabel_ms", ctypes.c_double), ("discharge_ms", ctypes.c_double),
+                ("rounds_by_size", ctypes.c_int64 * 4),
+                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["rounds_by_size"] = list(d["rounds_by_size"])
+        return d
 
 
 class _CSR(ctypes.Structure):
@@ -61,7 +65,8 @@ class GraphDesc(ctypes.Structure):
 _lib = None
 EXPORTS = ["mf_default_options", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
            "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
-           "mf_destroy_graph"]
+           "mf_solve_trace", "mf_destroy_graph", "mf_batch_create", "mf_batch_solve", "mf_batch_get_stats",
+           "mf_batch_destroy"]
 
 
 def lib():
@@ -86,8 +91,14 @@ def lib():
         L.mf_solve_device.argtypes = [vp, vp, vp, vp, vp]
         L.mf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.mf_run_rounds.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+        L.mf_solve_trace.argtypes = [vp, vp, vp, i64, vp]
         L.mf_destroy_graph.argtypes = [vp]
         L.mf_destroy_graph.restype = None
+        L.mf_batch_create.argtypes = [i32, vp, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+        L.mf_batch_solve.argtypes = [vp, vp, vp, vp]
+        L.mf_batch_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.mf_batch_destroy.argtypes = [vp]
+        L.mf_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -218,6 +229,15 @@ class Graph:
         """Outputs into torch CUDA tensors (int64[1], int32[m], int32/uint32[ceil(n/32)]), each optional."""
         _check(lib().mf_solve_device(self._h, _stream_ptr(stream), _ptr(value), _ptr(flow), _ptr(cut_bits)))
 
+    def solve_trace(self, capacity: int = 1 << 22):
+        """Per-round working-set sizes and relabel markers of one solve: (live int32[k], relabel int32[k])."""
+        live = np.zeros(capacity, np.int32)
+        gr = np.zeros(capacity, np.int32)
+        nr = ctypes.c_int64()
+        _check(lib().mf_solve_trace(self._h, _ptr(live), _ptr(gr), capacity, ctypes.byref(nr)))
+        k = min(int(nr.value), capacity)
+        return live[:k], gr[:k]
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().mf_get_stats(self._h, ctypes.byref(s)))
@@ -263,3 +283,62 @@ def solve_instance(inst, options: Options | None = None, flow=True, cut=True):
         fin = np.where(csr.arc_slot >= 0, r.flow[np.maximum(csr.arc_slot, 0)], 0).astype(np.int64)
     cut_b = cut_bits_to_bool(r.cut_bits, inst.n) if cut else None
     return r.value, fin, cut_b, csr, st
+
+
+def _descs(csrs, sts):
+    """GraphDesc array for (CSR, (s, t)) pairs; returns (array, keepalive)."""
+    arr = (GraphDesc * len(csrs))()
+    keep = []
+    for k, (c, (s, t)) in enumerate(zip(csrs, sts)):
+        row = np.ascontiguousarray(c.row_offsets, np.int64)
+        head = np.ascontiguousarray(c.head, np.int32)
+        cap = np.ascontiguousarray(c.cap, np.int32)
+        rev = np.ascontiguousarray(c.rev, np.int64)
+        keep += [row, head, cap, rev]
+        arr[k] = GraphDesc(c.n, c.m, row.ctypes.data, head.ctypes.data, cap.ctypes.data, rev.ctypes.data, s, t)
+    return arr, keep
+
+
+class Batch:
+    """Many independent instances solved by one persistent launch (mf_batch_*)."""
+
+    def __init__(self, csrs, sts, options: Options | None = None):
+        self.csrs = list(csrs)
+        self.sts = list(sts)
+        arr, keep = _descs(self.csrs, self.sts)
+        self._h = ctypes.c_void_p()
+        _check(lib().mf_batch_create(len(self.csrs), arr, ctypes.byref(options) if options else None,
+                                     ctypes.byref(self._h)))
+
+    def solve(self, flow=True, cut=True):
+        """Returns a list of Result (per-instance value, slot flows, cut bits)."""
+        k = len(self.csrs)
+        vals = np.zeros(k, np.int64)
+        flows = [np.zeros(c.m, np.int32) for c in self.csrs] if flow else None
+        cuts = [np.zeros((c.n + 31) // 32, np.uint32) for c in self.csrs] if cut else None
+        fp = (ctypes.c_void_p * k)(*[f.ctypes.data for f in flows]) if flow else None
+        cp = (ctypes.c_void_p * k)(*[c.ctypes.data for c in cuts]) if cut else None
+        _check(lib().mf_batch_solve(self._h, _ptr(vals), fp, cp))
+        return [Result(int(vals[i]), flows[i] if flow else None, cuts[i] if cut else None) for i in range(k)]
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().mf_batch_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().mf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,80 @@
+"""Batched solving (mf_batch_*): many independent instances in one persistent launch.
+
+Each instance's flow value and minimal source-side cut must equal the oracle's (they are unique), and
+each instance's flow must satisfy the flow definitions on its own arcs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_01926_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def check_batch(mf, insts, options=None):
+    csrs = [mf.build_csr(g.n, g.tail, g.head, g.cap) for g in insts]
+    with mf.Batch(csrs, [(g.s, g.t) for g in insts], options) as B:
+        res = B.solve()
+        st = B.stats()
+    for g, c, r in zip(insts, csrs, res):
+        ref = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False)
+        cut = mf.cut_bits_to_bool(r.cut_bits, g.n)
+        assert r.value == ref["value"], g.name
+        assert np.array_equal(cut, ref["cut"]), g.name
+        f_in = np.where(c.arc_slot >= 0, r.flow[np.maximum(c.arc_slot, 0)], 0).astype(np.int64)
+        assert not oracle.check_flow(g.n, g.s, g.t, g.tail, g.head, g.cap, f_in, r.value, cut), g.name
+    return res, st
+
+
+def test_batch_mixed_families(gpu):
+    insts = [I.grid2d(20, 30, 1), I.layered(10, 50, 2), I.random_graph(40, 300, 3, cap=(1, 40)),
+             I.grid3d(10, 9, 8, 4), I.rmat(9, 8, 5), I.multiframe(2, 6, side=20), I.grid2d(3, 3, 7)]
+    check_batch(gpu, insts)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_batch_many_uneven_layered(gpu, seed):
+    rng = np.random.default_rng(seed)
+    insts = [I.layered(int(rng.integers(2, 40)), int(rng.integers(1, 200)), 100 * seed + k) for k in range(40)]
+    check_batch(gpu, insts)
+
+
+def test_batch_equals_single_solves(gpu):
+    insts = [I.grid2d(33, 17, 11), I.layered(12, 64, 12), I.random_graph(100, 900, 13, cap=(1, 500))]
+    res, _ = check_batch(gpu, insts)
+    for g, r in zip(insts, res):
+        v, _, cut, _, _ = gpu.solve_instance(g)
+        assert v == r.value
+        assert np.array_equal(cut, gpu.cut_bits_to_bool(r.cut_bits, g.n))
+
+
+def test_batch_of_one_and_edge_instances(gpu):
+    from test_gpu_parity import EDGE_CASES
+
+    check_batch(gpu, [EDGE_CASES["direct_st"]])
+    check_batch(gpu, [EDGE_CASES[k] for k in sorted(EDGE_CASES)])
+
+
+def test_batch_cut_only(gpu):
+    insts = [I.grid2d(25, 25, 31), I.layered(8, 40, 32)]
+    csrs = [gpu.build_csr(g.n, g.tail, g.head, g.cap) for g in insts]
+    with gpu.Batch(csrs, [(g.s, g.t) for g in insts], gpu.default_options(cut_only=1)) as B:
+        res = B.solve(flow=False)
+    for g, r in zip(insts, res):
+        ref = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False)
+        assert r.value == ref["value"]
+        assert np.array_equal(gpu.cut_bits_to_bool(r.cut_bits, g.n), ref["cut"])
+
+
+def test_batch_rejects_bad_instance(gpu):
+    good = I.grid2d(5, 5, 1)
+    c = gpu.build_csr(good.n, good.tail, good.head, good.cap)
+    bad = gpu.CSR(c.n, c.row_offsets, c.head.copy(), c.cap, c.rev, c.arc_slot, 0)
+    bad.head[0] = c.n  # out of its instance
+    with pytest.raises(gpu.MFError) as e:
+        gpu.Batch([c, bad], [(good.s, good.t)] * 2)
+    assert e.value.code == -1
+    with pytest.raises(gpu.MFError) as e:
+        gpu.Batch([c], [(good.s, good.s)])
+    assert e.value.code == -3

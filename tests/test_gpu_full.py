@@ -1,0 +1,47 @@
+"""Full-size workloads on the GPU, in the launch configuration the bench uses (default options).
+
+The flow value and the minimal source-side cut must equal the oracle's stored results
+(tests/golden/*.json, written by tests/golden/make_golden.py from the oracle alone); the per-arc flow
+must satisfy the flow definitions (oracle.check_flow: capacity bounds, conservation, no residual s-t
+path, cut capacity = value, cut = residual reachability from s).
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_01926_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def digest(cut):
+    return hashlib.sha256(np.packbits(cut.astype(np.uint8), bitorder="little").tobytes()).hexdigest()
+
+
+@pytest.mark.parametrize("name", ["config0", "config1", "config2"])
+def test_full_size_against_golden(gpu, name):
+    gold = json.load(open(os.path.join(GOLD, f"{name}.json")))
+    g = getattr(I, name)()
+    assert (g.n, g.m, g.s, g.t) == (gold["n"], gold["m"], gold["s"], gold["t"]), "generator drifted"
+    value, flow, cut, csr, stats = gpu.solve_instance(g)
+    assert value == gold["value"]
+    assert int(cut.sum()) == gold["cut_size"]
+    assert digest(cut) == gold["cut_sha256"]
+    bad = oracle.check_flow(g.n, g.s, g.t, g.tail, g.head, g.cap, flow, value, cut)
+    assert not bad, bad
+
+
+def test_config1_cut_only_and_repeat(gpu):
+    gold = json.load(open(os.path.join(GOLD, "config1.json")))
+    g = I.config1()
+    csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
+    with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(cut_only=1)) as G:
+        for _ in range(2):
+            r = G.solve(flow=False)
+            assert r.value == gold["value"]
+            assert digest(gpu.cut_bits_to_bool(r.cut_bits, g.n)) == gold["cut_sha256"]
