@@ -110,10 +110,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def load_workload():
+def load_workload(shape=None):
     from paper_1507_01926_gb300 import inputs, mf
 
-    g = inputs.config1()
+    if shape is None or tuple(shape) == (256, 256, 128):
+        g = inputs.config1()
+    else:
+        g = inputs.grid3d(*shape, seed=inputs.BASE_SEED + 1)
     csr = mf.build_csr(g.n, g.tail, g.head, g.cap)
     return g, csr
 
@@ -184,6 +187,117 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """configs[3]: a batch of uneven layered graphs. Batched = all instances in one persistent launch
+    (mf_batch_solve); plain = one mf_solve launch per instance on the same GPU, timed on the first
+    --plain-count instances. Reports solves/s for both and their ratio."""
+    import torch
+
+    from paper_1507_01926_gb300 import inputs, mf
+
+    torch.cuda.set_device(0)
+    params = inputs.config3_params(args.batch_count)
+    t0 = time.perf_counter()
+    insts = [inputs.config3_instance(i, L, W) for i, (L, W) in enumerate(params)]
+    csrs = [mf.build_csr(g.n, g.tail, g.head, g.cap) for g in insts]
+    sts = [(g.s, g.t) for g in insts]
+    prep_s = time.perf_counter() - t0
+    nv, ns = sum(g.n for g in insts), sum(c.m for c in csrs)
+    # plain: one launch per instance, graphs already resident
+    k = min(args.plain_count, len(insts))
+    graphs = [mf.Graph.from_csr(c, s, t) for c, (s, t) in zip(csrs[:k], sts[:k])]
+    for G in graphs[: min(3, k)]:
+        G.solve(flow=False, cut=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_vals = [G.solve(flow=False, cut=False).value for G in graphs]
+    plain_s = time.perf_counter() - t0
+    for G in graphs:
+        G.close()
+    # batched: the same first k instances, then the whole batch
+    with mf.Batch(csrs[:k], sts[:k]) as B:
+        B.solve(flow=False, cut=False)
+        t0 = time.perf_counter()
+        sub = B.solve(flow=False, cut=False)
+        sub_s = time.perf_counter() - t0
+    assert [r.value for r in sub] == plain_vals
+    with mf.Batch(csrs, sts) as B:
+        B.solve(flow=False, cut=False)
+        times = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            res = B.solve(flow=False, cut=False)
+            times.append(time.perf_counter() - t0)
+        st = B.stats()
+    full_s = statistics.median(times)
+    line = {"metric": "batched solves/s (layered batch)", "value": len(insts) / full_s, "unit": "solves/s",
+            "n_gpus": 1, "steps": len(times), "warmup": 1, "ms_per_step": 1000 * full_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+            "config": {"workload": f"{len(insts)} layered graphs L~logU[16,256], W~logU[64,4096]", "vertices": nv,
+                       "slots": ns},
+            "plain": {"instances": k, "solves_per_s": k / plain_s, "seconds": plain_s},
+            "batched_same_instances": {"instances": k, "solves_per_s": k / sub_s, "seconds": sub_s},
+            "speedup_batched_vs_plain": (k / sub_s) / (k / plain_s),
+            "speedup_full_batch_vs_plain": (len(insts) / full_s) / (k / plain_s),
+            "rounds": st["rounds"], "global_relabels": st["global_relabels"], "host_prep_s": prep_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """configs[4]: a Poisson stream of 2D-grid and multi-frame requests through the continuous-batching
+    service under a 64 GB budget. First the saturated throughput X (all requests submitted at once), then
+    the stream at 0.7 X and 1.0 X; reports p50/p99 latency and solves/s."""
+    import torch
+
+    from paper_1507_01926_gb300 import inputs, mf
+
+    torch.cuda.set_device(0)
+    reqs = inputs.config4_requests(args.requests, rate_per_s=1.0)
+    t0 = time.perf_counter()
+    items = []
+    for i, (_, kind, size) in enumerate(reqs):
+        g = inputs.config4_instance(i, kind, size)
+        items.append((g, mf.build_csr(g.n, g.tail, g.head, g.cap)))
+    prep_s = time.perf_counter() - t0
+    budget = 64 << 30
+
+    def run(rate):
+        arrivals = [a / rate for a, _, _ in reqs] if rate else [0.0] * len(reqs)
+        with mf.Service(budget) as svc:
+            t_start = time.perf_counter()
+            tickets = []
+            for (g, c), at in zip(items, arrivals):
+                now = time.perf_counter() - t_start
+                if at > now:
+                    time.sleep(at - now)
+                tickets.append(svc.submit(c, g.s, g.t))
+            lat = [svc.wait(t) for t in tickets]
+            wall = time.perf_counter() - t_start
+            vals = [svc.poll(t, flow=False, cut=False).value for t in tickets]
+        return lat, wall, vals
+
+    lat0, wall0, vals0 = run(None)
+    X = len(reqs) / wall0
+    out = {"saturated": {"solves_per_s": X, "p50_ms": float(np.percentile(lat0, 50)),
+                         "p99_ms": float(np.percentile(lat0, 99))}}
+    for frac in (0.7, 1.0):
+        lat, wall, vals = run(frac * X)
+        assert vals == vals0
+        out[f"{frac:.1f}X"] = {"rate_per_s": frac * X, "solves_per_s": len(reqs) / wall,
+                               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    nv = sum(g.n for g, _ in items)
+    line = {"metric": "served solves/s with p50/p99 latency (Poisson stream)", "value": out["0.7X"]["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
+            "ms_per_step": 1000.0 / out["0.7X"]["solves_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+            "config": {"workload": f"first {len(reqs)} requests of the 2D-grid / multi-frame stream", "vertices": nv,
+                       "budget_bytes": budget},
+            "latency": out, "host_prep_s": prep_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,9 +306,19 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid3d", type=int, nargs=3, default=[256, 256, 128], metavar=("X", "Y", "Z"),
+                    help="size of the 3D grid workload (profiling runs use a smaller case)")
+    ap.add_argument("--workload", default="grid3d", choices=["grid3d", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--plain-count", type=int, default=128)
+    ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
 
@@ -216,7 +340,7 @@ def main():
         torch.distributed.barrier()
     from paper_1507_01926_gb300 import mf
 
-    g, csr = load_workload()
+    g, csr = load_workload(args.grid3d)
     opt = mf.default_options(device=torch.cuda.current_device())
     stream = torch.cuda.Stream()
     row = torch.from_numpy(csr.row_offsets).to(dev)
@@ -266,7 +390,7 @@ def main():
         total_ms_max, scans_all = total_ms, float(scans)
     value = scans_all / (total_ms_max / 1000.0)
     flow_value = int(val.item())
-    gold = golden_value()
+    gold = golden_value() if tuple(args.grid3d) == (256, 256, 128) else None
 
     # roofline of the (only) kernel: the persistent solve kernel, one launch per step
     peak, peak_kind = peaks()
@@ -292,7 +416,7 @@ def main():
     import ctypes
 
     L = mf.lib()
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = ctypes.c_void_p()
@@ -310,9 +434,11 @@ def main():
             e2e_scans += s.scans_discharge + s.scans_bfs
     h2d = 8 * (g.n + 1) + 4 * csr.m + 4 * csr.m + 8 * csr.m
     d2h = 8 + 4 * csr.m + 4 * ((g.n + 31) // 32)
-    e2e = {"value": e2e_scans / sum(e2e_t), "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": 1000 * statistics.mean(e2e_t),
-           "includes": "mf_create_graph (H2D from pinned memory + on-device validation) + mf_solve (flow, cut D2H)"}
+    e2e = None
+    if e2e_t:
+        e2e = {"value": e2e_scans / sum(e2e_t), "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * statistics.mean(e2e_t),
+               "includes": "mf_create_graph (H2D from pinned memory + on-device validation) + mf_solve (flow, cut D2H)"}
 
     cpu = None if args.no_cpu_baseline else cpu_baseline(g)
     clocks = clk.summary()
@@ -320,7 +446,8 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "slots": csr.m, "arcs": g.m, "global_batch": world,
+        "config": {"workload": WORKLOAD if tuple(args.grid3d) == (256, 256, 128) else g.name,
+                   "n": g.n, "slots": csr.m, "arcs": g.m, "global_batch": world,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (about 1.3 GB of device state per solve)"},
         "solve_ms": statistics.median(per_step), "solve_ms_all": [round(x, 3) for x in per_step],

@@ -109,6 +109,9 @@ typedef struct mf_stats {
   double relabel_ms;        /* time in global relabels (BFS + working-set rebuild) */
   double discharge_ms;      /* time in push-relabel rounds */
   int64_t rounds_by_size[4]; /* rounds whose working set had <1K, <16K, <256K, more vertices */
+  /* CTA 0's view of where round and BFS-level time goes (ms): its own work,
+   * the list flush and reductions, and the wait at the grid barrier */
+  double round_work_ms, round_tail_ms, round_wait_ms, level_work_ms, level_wait_ms;
   int32_t grid_blocks;      /* persistent-kernel CTAs */
   int32_t block_threads;
 } mf_stats;
@@ -223,6 +226,30 @@ int mf_batch_create(int32_t count, const mf_graph_desc *descs, const mf_options 
 int mf_batch_solve(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits);
 int mf_batch_get_stats(const mf_batch *b, mf_stats *out);
 void mf_batch_destroy(mf_batch *b);
+
+/*
+ * Serving with continuous batching. mf_service_create starts worker lanes on
+ * opt->device (each lane: a host thread, a CUDA stream and a share of the
+ * SMs). mf_submit copies the instance (host arrays, paired-slot CSR) and
+ * returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
+ * exceed device_budget_bytes (its estimated device footprint is 61 bytes per
+ * vertex + 32 bytes per slot). Lanes admit queued requests in arrival order
+ * while the resident footprint stays within the budget, solve each admitted
+ * group in one persistent launch, and keep the results. A request that
+ * arrives while others are solving starts on the next free lane.
+ * mf_poll returns MF_PENDING until the ticket's result is ready, then the
+ * result (outputs as for mf_solve, each nullable; the solve's error code if it
+ * failed) and forgets the ticket. mf_wait blocks until the ticket is done
+ * (timeout_ms < 0: no limit; MF_PENDING on timeout) without consuming it, and
+ * reports the time from submission to completion. Unknown tickets give
+ * MF_ERR_UNKNOWN_TICKET. mf_service_destroy waits for running solves and drops
+ * queued requests.
+ */
+int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_service **out);
+int mf_submit(mf_service *svc, const mf_graph_desc *g, mf_ticket *out);
+int mf_poll(mf_service *svc, mf_ticket ticket, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_bits);
+int mf_wait(mf_service *svc, mf_ticket ticket, int32_t timeout_ms, double *latency_ms);
+void mf_service_destroy(mf_service *svc);
 
 #ifdef __cplusplus
 }

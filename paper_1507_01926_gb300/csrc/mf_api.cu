@@ -27,7 +27,7 @@ int fail(int code, const char *fmt, ...) {
 
 void clear_error() { g_err.clear(); }
 
-const char *last_error() { return g_err.c_str(); }
+const char *last_error() { return g_err.c_str(); }  // calling thread's message
 
 int cuda_fail(cudaError_t e, const char *what) {
   if (e == cudaErrorMemoryAllocation) {
@@ -300,6 +300,11 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   s.relabel_ms = (double)c.t_gr * 1e-6;
   s.discharge_ms = (double)c.t_dis * 1e-6;
   for (int i = 0; i < 4; i++) s.rounds_by_size[i] = c.rounds_by_size[i];
+  s.round_work_ms = (double)c.t_rwork * 1e-6;
+  s.round_tail_ms = (double)c.t_rtail * 1e-6;
+  s.round_wait_ms = (double)c.t_rwait * 1e-6;
+  s.level_work_ms = (double)c.t_lwork * 1e-6;
+  s.level_wait_ms = (double)c.t_lwait * 1e-6;
   s.preflow_ms = c.t_preflow > c.t_start ? (double)(c.t_preflow - c.t_start) * 1e-6 : 0.0;
   s.grid_blocks = g->grid;
   s.block_threads = g->block;

@@ -182,6 +182,8 @@ int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cu
   return MF_OK;
 }
 
+mf_batch *new_batch() { return new mf_batch(); }
+
 void destroy_union(mf_batch *b) {
   if (!b) return;
   if (b->g) mf_destroy_graph(b->g);

@@ -30,6 +30,8 @@ struct Ctl {
   long long scans_dis, scans_bfs, pushes, relabels;
   long long visits_dis, visits_bfs;
   unsigned long long t_gr, t_dis;            // ns in global relabels / rounds (CTA 0's view)
+  unsigned long long t_rwork, t_rtail, t_rwait;  // rounds, CTA 0: own discharge work, list flush + sums, barrier wait
+  unsigned long long t_lwork, t_lwait;       // BFS levels, CTA 0: own expansion work, barrier wait
   long long rounds_by_size[4];               // rounds with <1K, <16K, <256K, more list entries
   unsigned long long t_start, t_preflow, t_end;  // %globaltimer, ns
   int stopped_round;   // MODE_ROUNDS: rounds run

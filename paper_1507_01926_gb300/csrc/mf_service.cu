@@ -1,0 +1,270 @@
+// Serving (mf_service_*, mf_submit, mf_poll, mf_wait): continuous batching of
+// max-flow requests on one GPU.
+//
+// Requests are copied at submission and queued. Worker lanes (host threads,
+// each with its own CUDA stream and a share of the SMs for its persistent
+// launches) admit queued requests in arrival order while their estimated
+// device footprint fits the memory budget, pack them into one instance-offset
+// union (mf_batch machinery) and solve it. A request that arrives while other
+// requests are on the GPU is admitted by the next free lane as soon as memory
+// allows, so its solve overlaps with the ones already running. Results stay
+// with the service until mf_poll hands them out.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "mf.h"
+#include "mf_internal.h"
+
+using namespace mf;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  mf_ticket id = 0;
+  int n = 0, s = 0, t = 0;
+  long long m = 0;
+  std::vector<int64_t> row, rev;
+  std::vector<int32_t> head, cap;
+  size_t bytes = 0;
+  Clock::time_point t_submit, t_done;
+  bool done = false;
+  int rc = MF_OK;
+  std::string err;
+  int64_t value = 0;
+  std::vector<int32_t> flow;
+  std::vector<uint32_t> cut;
+};
+
+// Device bytes one request occupies while resident (vertex state, slot
+// arrays, staging during creation, outputs).
+size_t footprint(long long n, long long m) { return (size_t)(61 * n + 32 * m + 65536); }
+
+}  // namespace
+
+struct mf_service {
+  size_t budget = 0;
+  mf_options opt{};
+  int lanes = 2;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request *> pending;
+  std::unordered_map<mf_ticket, Request *> tickets;
+  size_t in_use = 0;
+  long long resident_n = 0, resident_m = 0;
+  mf_ticket next_id = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+};
+
+namespace mf {
+int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *opt, cudaStream_t stream,
+                 mf_batch *b);
+int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits);
+mf_batch *new_batch();
+void destroy_union(mf_batch *b);
+const char *last_error();
+}  // namespace mf
+
+static void lane_main(mf_service *svc, int lane) {
+  mf_options o = svc->opt;
+  cudaSetDevice(o.device);
+  cudaStream_t stream = nullptr;
+  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  for (;;) {
+    std::vector<Request *> batch;
+    size_t bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(svc->mu);
+      svc->cv_work.wait(lk, [&] {
+        return svc->stop ||
+               (!svc->pending.empty() && svc->in_use + svc->pending.front()->bytes <= svc->budget);
+      });
+      if (svc->stop) break;
+      long long nn = 0, mm = 0;
+      while (!svc->pending.empty()) {
+        Request *r = svc->pending.front();
+        if (svc->in_use + bytes + r->bytes > svc->budget) break;
+        if (svc->resident_n + nn + r->n > UNV - 4 || svc->resident_m + mm + r->m > 2147483646LL) break;
+        bytes += r->bytes;
+        nn += r->n;
+        mm += r->m;
+        batch.push_back(r);
+        svc->pending.pop_front();
+      }
+      svc->in_use += bytes;
+      svc->resident_n += nn;
+      svc->resident_m += mm;
+      if (!svc->pending.empty()) svc->cv_work.notify_one();  // another lane may take the rest
+    }
+    std::vector<mf_graph_desc> descs(batch.size());
+    for (size_t i = 0; i < batch.size(); i++) {
+      Request *r = batch[i];
+      descs[i] = mf_graph_desc{r->n, r->m, r->row.data(), r->head.data(), r->cap.data(), r->rev.data(), r->s, r->t};
+      r->flow.assign((size_t)r->m, 0);
+      r->cut.assign(((size_t)r->n + 31) / 32, 0);
+    }
+    std::vector<int64_t> values(batch.size(), 0);
+    std::vector<int32_t *> fl(batch.size());
+    std::vector<uint32_t *> cu(batch.size());
+    for (size_t i = 0; i < batch.size(); i++) {
+      fl[i] = batch[i]->flow.data();
+      cu[i] = batch[i]->cut.data();
+    }
+    mf_batch *b = new_batch();
+    int rc = create_union((int32_t)batch.size(), descs.data(), &o, stream, b);
+    if (rc == MF_OK) rc = solve_union(b, values.data(), fl.data(), cu.data());
+    std::string err = rc ? std::string(last_error()) : std::string();
+    destroy_union(b);
+    long long nn = 0, mm = 0;
+    {
+      std::lock_guard<std::mutex> lk(svc->mu);
+      const auto now = Clock::now();
+      for (size_t i = 0; i < batch.size(); i++) {
+        Request *r = batch[i];
+        r->value = values[i];
+        r->rc = rc;
+        r->err = err;
+        r->done = true;
+        r->t_done = now;
+        nn += r->n;
+        mm += r->m;
+        // the instance itself is no longer needed
+        std::vector<int64_t>().swap(r->row);
+        std::vector<int64_t>().swap(r->rev);
+        std::vector<int32_t>().swap(r->head);
+        std::vector<int32_t>().swap(r->cap);
+      }
+      svc->in_use -= bytes;
+      svc->resident_n -= nn;
+      svc->resident_m -= mm;
+    }
+    svc->cv_done.notify_all();
+    svc->cv_work.notify_all();
+  }
+  if (stream) cudaStreamDestroy(stream);
+}
+
+extern "C" {
+
+int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_service **out) {
+  clear_error();
+  if (!out) return fail(MF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (device_budget_bytes < (1u << 20)) return fail(MF_ERR_INVALID_ARG, "budget must be at least 1 MiB");
+  mf_options o;
+  if (opt)
+    o = *opt;
+  else
+    mf_default_options(&o);
+  int rc = check_options(&o);
+  if (rc) return rc;
+  cudaError_t e = cudaSetDevice(o.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  int bps = 0;
+  if (solver_occupancy(o.block_threads, &bps) || bps < 1)
+    return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", o.block_threads);
+  mf_service *svc = new mf_service();
+  svc->budget = device_budget_bytes;
+  svc->lanes = bps >= 2 ? 2 : 1;
+  o.blocks_per_sm = bps / svc->lanes;  // each lane's launches take its share of every SM
+  svc->opt = o;
+  for (int k = 0; k < svc->lanes; k++) svc->workers.emplace_back(lane_main, svc, k);
+  *out = svc;
+  return MF_OK;
+}
+
+int mf_submit(mf_service *svc, const mf_graph_desc *g, mf_ticket *out) {
+  clear_error();
+  if (!svc || !g || !out) return fail(MF_ERR_INVALID_ARG, "NULL argument");
+  if (g->n < 2 || g->m < 0) return fail(MF_ERR_INVALID_ARG, "n must be >= 2 and m >= 0");
+  if (!g->row_offsets || (g->m > 0 && (!g->head || !g->cap || !g->rev))) return fail(MF_ERR_INVALID_ARG, "NULL array");
+  if (g->s < 0 || g->s >= g->n || g->t < 0 || g->t >= g->n) return fail(MF_ERR_INVALID_ARG, "s or t out of range");
+  if (g->s == g->t) return fail(MF_ERR_S_EQ_T, "source equals sink");
+  const size_t bytes = footprint(g->n, g->m);
+  if (bytes > svc->budget)
+    return fail(MF_ERR_OVER_BUDGET, "instance needs about %zu bytes, budget is %zu", bytes, svc->budget);
+  Request *r = new Request();
+  r->n = g->n;
+  r->m = g->m;
+  r->s = g->s;
+  r->t = g->t;
+  r->bytes = bytes;
+  r->row.assign(g->row_offsets, g->row_offsets + g->n + 1);
+  r->head.assign(g->head, g->head + g->m);
+  r->cap.assign(g->cap, g->cap + g->m);
+  r->rev.assign(g->rev, g->rev + g->m);
+  {
+    std::lock_guard<std::mutex> lk(svc->mu);
+    r->id = svc->next_id++;
+    r->t_submit = Clock::now();
+    svc->tickets[r->id] = r;
+    svc->pending.push_back(r);
+  }
+  svc->cv_work.notify_one();
+  *out = r->id;
+  return MF_OK;
+}
+
+int mf_wait(mf_service *svc, mf_ticket ticket, int32_t timeout_ms, double *latency_ms) {
+  clear_error();
+  if (!svc) return fail(MF_ERR_INVALID_ARG, "service is NULL");
+  std::unique_lock<std::mutex> lk(svc->mu);
+  auto it = svc->tickets.find(ticket);
+  if (it == svc->tickets.end()) return fail(MF_ERR_UNKNOWN_TICKET, "unknown ticket %lld", (long long)ticket);
+  Request *r = it->second;
+  if (timeout_ms < 0)
+    svc->cv_done.wait(lk, [&] { return r->done; });
+  else if (!svc->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
+    return MF_PENDING;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  return MF_OK;
+}
+
+int mf_poll(mf_service *svc, mf_ticket ticket, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_bits) {
+  clear_error();
+  if (!svc) return fail(MF_ERR_INVALID_ARG, "service is NULL");
+  Request *r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(svc->mu);
+    auto it = svc->tickets.find(ticket);
+    if (it == svc->tickets.end()) return fail(MF_ERR_UNKNOWN_TICKET, "unknown ticket %lld", (long long)ticket);
+    r = it->second;
+    if (!r->done) return MF_PENDING;
+    svc->tickets.erase(it);
+  }
+  int rc = r->rc;
+  if (rc == MF_OK) {
+    if (flow_value) *flow_value = r->value;
+    if (arc_flow && r->m > 0) memcpy(arc_flow, r->flow.data(), (size_t)r->m * 4);
+    if (cut_bits) memcpy(cut_bits, r->cut.data(), r->cut.size() * 4);
+  } else {
+    fail(rc, "%s", r->err.c_str());
+  }
+  delete r;
+  return rc;
+}
+
+void mf_service_destroy(mf_service *svc) {
+  if (!svc) return;
+  {
+    std::lock_guard<std::mutex> lk(svc->mu);
+    svc->stop = true;
+  }
+  svc->cv_work.notify_all();
+  for (auto &t : svc->workers) t.join();
+  for (auto &kv : svc->tickets) delete kv.second;
+  delete svc;
+}
+
+}  // extern "C"

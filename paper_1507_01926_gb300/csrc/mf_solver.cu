@@ -156,13 +156,50 @@ __device__ __forceinline__ long long warp_incl_scan(long long x, int lane) {
   return x;
 }
 
+constexpr int QCAP = 2048;  // per-CTA staging of list appends
+
 struct Shared {
   unsigned long long bars;  // grid barriers passed by this CTA
   int pick;
   int flag;
+  int qn;                   // staged appends (may exceed QCAP; the excess went straight to the list)
+  int qbase;
   int imin[MAX_WARPS];
   long long lsum[MAX_WARPS];
+  int qbuf[QCAP];
 };
+
+// Stages one append to the list of generation gen in shared memory; qflush
+// publishes the CTA's staged entries with one global atomic.
+__device__ __forceinline__ void qpush(const Dev &D, Shared &sh, int gen, int val) {
+  const int i = atomicAdd(&sh.qn, 1);
+  if (i < QCAP)
+    sh.qbuf[i] = val;
+  else
+    append(D, gen, val);
+}
+
+// All threads of the CTA call this at the end of a phase that appended to gen.
+__device__ void qflush(const Dev &D, Shared &sh, int gen) {
+  __syncthreads();
+  const int k = min(sh.qn, QCAP);
+  if (k > 0) {
+    if (threadIdx.x == 0) sh.qbase = atomicAdd(&D.ctl->cnt[gen & 3], k);
+    __syncthreads();
+    const int base = sh.qbase;
+    int *L = list_of(D, gen);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const int idx = base + i;
+      if (idx < D.n)
+        L[idx] = sh.qbuf[i];
+      else
+        set_err(D, MF_ERR_INTERNAL, 11);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh.qn = 0;
+  __syncthreads();
+}
 
 // Block-wide sum of a 64-bit value (all threads call; result valid in all).
 __device__ long long block_sum(long long x, Shared &sh) {
@@ -236,12 +273,12 @@ __device__ __forceinline__ bool deliver(const Dev &D, const RoundCtx &R, int w, 
   return atomicExch(act_ptr(D, w, R.p ^ 1), R.r + 1) != R.r + 1;
 }
 
-__device__ __forceinline__ void finish_vertex(const Dev &D, const RoundCtx &R, int v, int dp, long long ex,
-                                              int cap_v) {
+__device__ __forceinline__ void finish_vertex(const Dev &D, Shared &sh, const RoundCtx &R, int v, int dp,
+                                              long long ex, int cap_v) {
   *lab_ptr(D, v, R.p ^ 1) = dp;
   D.e[v] = ex;
   if (ex > 0 && dp < cap_v) {
-    if (atomicExch(act_ptr(D, v, R.p ^ 1), R.r + 1) != R.r + 1) append(D, R.next, v);
+    if (atomicExch(act_ptr(D, v, R.p ^ 1), R.r + 1) != R.r + 1) qpush(D, sh, R.next, v);
   }
 }
 
@@ -256,10 +293,11 @@ __device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_
 }
 
 // One thread, deg <= KT: arcs cached in registers for all passes.
-__device__ void discharge_thread(const Dev &D, const RoundCtx &R, int v, int beg, int deg, int dv, int cap_v,
-                                 TStat &st, long long &work) {
+__device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, int v, int beg, int deg, int dv,
+                                 int cap_v, TStat &st, long long &work) {
   int wv[KT], rs[KT], dw[KT];
   unsigned act = 0;
+  long long ex = __ldcg(&D.e[v]) + take_added(D, v);
 #pragma unroll
   for (int i = 0; i < KT; i++) {
     wv[i] = 0;
@@ -277,7 +315,6 @@ __device__ void discharge_thread(const Dev &D, const RoundCtx &R, int v, int beg
       dw[i] = lab_of(x, R.p);
       if (act_of(x, R.p) == R.r) act |= 1u << i;
     }
-  long long ex = __ldcg(&D.e[v]) + take_added(D, v);
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
@@ -316,15 +353,15 @@ __device__ void discharge_thread(const Dev &D, const RoundCtx &R, int v, int beg
     work += deg + D.beta;
     if (dp >= cap_v) break;
   }
-  finish_vertex(D, R, v, dp, ex, cap_v);
+  finish_vertex(D, sh, R, v, dp, ex, cap_v);
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if ((found >> i) & 1u) append(D, R.next, wv[i]);
+    if ((found >> i) & 1u) qpush(D, sh, R.next, wv[i]);
   flush_sink(D, sink, to_sink);
 }
 
 // One warp (all 32 lanes call), arcs in chunks of 32.
-__device__ void discharge_warp(const Dev &D, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
+__device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
                                long long &work) {
   const int lane = threadIdx.x & 31;
   const int beg = __ldg(&D.row[v]);
@@ -374,7 +411,7 @@ __device__ void discharge_warp(const Dev &D, const RoundCtx &R, int v, int dv, i
           found = deliver(D, R, w, wact, delta);
         }
       }
-      if (found) append(D, R.next, w);
+      if (found) qpush(D, sh, R.next, w);
       if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
       skipped |= (__ballot_sync(FULL, skip) != 0);
       ex = total >= ex ? 0 : ex - total;
@@ -388,7 +425,7 @@ __device__ void discharge_warp(const Dev &D, const RoundCtx &R, int v, int dv, i
     }
     if (dp >= cap_v) break;
   }
-  if (lane == 0) finish_vertex(D, R, v, dp, ex, cap_v);
+  if (lane == 0) finish_vertex(D, sh, R, v, dp, ex, cap_v);
   __syncwarp();
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncwarp();
@@ -455,7 +492,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
           found = deliver(D, R, w, wact, delta);
         }
       }
-      if (found) append(D, R.next, w);
+      if (found) qpush(D, sh, R.next, w);
       if (resid && !skip && rs > 0 && dw >= dp) newl = min(newl, dw + 1);
       if (skip) sh.flag = 1;
       __syncthreads();
@@ -477,7 +514,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
     }
     if (dp >= cap_v) break;
   }
-  if (threadIdx.x == 0) finish_vertex(D, R, v, dp, ex, cap_v);
+  if (threadIdx.x == 0) finish_vertex(D, sh, R, v, dp, ex, cap_v);
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncthreads();
 }
@@ -491,46 +528,49 @@ __device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int
   if (ad) D.e[v] = __ldcg(&D.e[v]) + ad;
 }
 
-// One round: (1) merge step of the previous round for its vertices that are
-// not in this working set (label carried into the next slot, addedExcess
-// folded into the excess); (2) discharge every vertex of this working set
-// (list generation gen), discoveries to generation gen + 1.
-__device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, long long rnd, TStat &st) {
+// One round over a combined index space: entries [0, count) are the working
+// set of this round (list generation gen), discharged; entries [count, count +
+// cp) are the previous working set, whose members that are not in this one get
+// the merge step of the previous round (label carried into the next slot,
+// addedExcess folded into the excess). Both kinds run side by side on
+// different threads. Discoveries go to generation gen + 1.
+__device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, long long rnd, TStat &st,
+                            unsigned long long &t_phase0) {
   const RoundCtx R{r, r & 1, gen + 1};
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.ctl->cnt[(gen + 2) & 3] = 0;
     D.ctl->work[(rnd + 1) % 3] = 0;
   }
-  if (prev_valid) {
-    const int *P = list_of(D, gen - 1);
-    const int cp = list_count(D, gen - 1);
-    for (int i = tid; i < cp; i += nthr) {
-      const int u = __ldcg(&P[i]);
-      if (__ldcg(act_ptr(D, u, R.p)) == r) continue;  // in this working set: handled below
-      *lab_ptr(D, u, R.p ^ 1) = __ldcg(lab_ptr(D, u, R.p));
-      const long long ad = take_added(D, u);
-      if (ad) atomic_add64(&D.e[u], ad);  // excess of a non-member may receive pushes now
-    }
-  }
   const int *W = list_of(D, gen);
   const int count = list_count(D, gen);
+  const int *P = list_of(D, gen - 1);
+  const int cp = prev_valid ? list_count(D, gen - 1) : 0;
+  const int total = count + cp;
   const int lane = threadIdx.x & 31;
   long long work = 0;
-  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
     const int idx = base + threadIdx.x;
-    const int v = idx < count ? __ldcg(&W[idx]) : -1;
-    int beg = 0, deg = 0, cls = 0, dv = 0, cap_v = 0;
-    if (v >= 0) {
+    int v = -1, beg = 0, deg = 0, cls = 0, dv = 0, cap_v = 0;
+    if (idx < count) {
+      v = __ldcg(&W[idx]);
       dv = __ldcg(lab_ptr(D, v, R.p));
       cap_v = cap_of(D, v);
       if (dv >= cap_v) {
         retire_dead(D, R, v, dv);
+        v = -1;
       } else {
         beg = __ldg(&D.row[v]);
         deg = __ldg(&D.row[v + 1]) - beg;
         cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
         st.visits_dis++;
+      }
+    } else if (idx < total) {
+      const int u = __ldcg(&P[idx - count]);
+      const int4 x = __ldcg(&D.vs[u]);
+      if (act_of(x, R.p) != r) {  // not in this working set
+        *lab_ptr(D, u, R.p ^ 1) = lab_of(x, R.p);
+        const long long ad = take_added(D, u);
+        if (ad) atomic_add64(&D.e[u], ad);  // the excess of a non-member may receive pushes now
       }
     }
     for (;;) {  // CTA per vertex
@@ -558,13 +598,22 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       const int pdv = __shfl_sync(FULL, dv, leader);
       const int pcap = __shfl_sync(FULL, cap_v, leader);
       if (lane == leader) cls = 0;
-      discharge_warp(D, R, pv, pdv, pcap, st, work);
+      discharge_warp(D, sh, R, pv, pdv, pcap, st, work);
     }
-    if (cls == 1) discharge_thread(D, R, v, beg, deg, dv, cap_v, st, work);
+    if (cls == 1) discharge_thread(D, sh, R, v, beg, deg, dv, cap_v, st, work);
     __syncwarp();
   }
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const unsigned long long t1 = timer ? gtimer() : 0;
+  qflush(D, sh, R.next);
   const long long wsum = block_sum(work, sh);
   if (threadIdx.x == 0 && wsum) atomic_add64(&D.ctl->work[rnd % 3], wsum);
+  if (timer) {
+    const unsigned long long t2 = gtimer();
+    D.ctl->t_rwork += t1 - t_phase0;
+    D.ctl->t_rtail += t2 - t1;
+    t_phase0 = t2;
+  }
 }
 
 // ------------------------------------------------------------------ BFS
@@ -575,17 +624,18 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
 // forward BFS for the cut: res[a] = c_f(v, w)) and CAS(label(w): UNV -> k + 1)
 // succeeds.
 
-__device__ __forceinline__ void bfs_arc(const Dev &D, int a, int lvl, bool reverse, int next) {
+__device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int lvl, bool reverse, int next) {
   const int w = __ldg(&D.head[a]);
   const int2 x = __ldcg(&D.rr[a]);
   const int cf = reverse ? x.y : x.x;
   if (cf > 0 && __ldcg(lab_ptr(D, w, 0)) == UNV) {
-    if (atomicCAS(lab_ptr(D, w, 0), UNV, lvl + 1) == UNV) append(D, next, w);
+    if (atomicCAS(lab_ptr(D, w, 0), UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
   }
 }
 
 // One thread, deg <= KT, loads issued together.
-__device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int lvl, bool reverse, int next) {
+__device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, int deg, int lvl, bool reverse,
+                                           int next) {
   int w[KT], cf[KT], lab[KT];
 #pragma unroll
   for (int i = 0; i < KT; i++) {
@@ -601,7 +651,7 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, int beg, int deg, int l
   for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(lab_ptr(D, w[i], 0)) : 0;
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) == UNV) append(D, next, w[i]);
+    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) == UNV) qpush(D, sh, next, w[i]);
 }
 
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
@@ -630,7 +680,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       if (pv < 0) break;
       if (v == pv) cls = 0;
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, a, lvl, reverse, next);
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, sh, a, lvl, reverse, next);
       __syncthreads();
     }
     for (;;) {
@@ -640,12 +690,13 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       const int pv = __shfl_sync(FULL, v, leader);
       if (lane == leader) cls = 0;
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + lane; a < e; a += 32) bfs_arc(D, a, lvl, reverse, next);
+      for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, lvl, reverse, next);
       __syncwarp();
     }
-    if (cls == 1) bfs_thread(D, beg, deg, lvl, reverse, next);
+    if (cls == 1) bfs_thread(D, sh, beg, deg, lvl, reverse, next);
     __syncwarp();
   }
+  qflush(D, sh, next);
 }
 
 // BFS from `seeds` (label 0) on label slot 0. `blockers` get UNV + 1 and are
@@ -664,11 +715,12 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
       const int d = __ldcg(lab_ptr(D, v, 0));
       if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) > 0) {
         x = 0;
-        append(D, next, v);
+        qpush(D, sh, next, v);
       }
     }
     *lab_ptr(D, v, 0) = x;
   }
+  qflush(D, sh, next);
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
@@ -679,12 +731,19 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     for (int i = threadIdx.x; i < nterm; i += blockDim.x) append(D, next, seeds[i]);
   if (!grid_sync(D, sh, where)) return false;
   gen++;
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   for (int lvl = 0;; lvl++) {
     if (list_count(D, gen) == 0) break;
+    const unsigned long long t0 = timer ? gtimer() : 0;
     bfs_level(D, sh, gen, lvl, reverse, st);
+    const unsigned long long t1 = timer ? gtimer() : 0;
     if (!grid_sync(D, sh, where)) return false;
     gen++;
-    if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->levels++;
+    if (timer) {
+      D.ctl->levels++;
+      D.ctl->t_lwork += t1 - t0;
+      D.ctl->t_lwait += gtimer() - t1;
+    }
   }
   return true;
 }
@@ -718,9 +777,10 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     }
     if (d > 0 && d < c && ev > 0) {
       *act_ptr(D, v, p) = r;
-      append(D, next, v);
+      qpush(D, sh, next, v);
     }
   }
+  qflush(D, sh, next);
   if (!grid_sync(D, sh, 3)) return false;
   gen++;
   return true;
@@ -786,9 +846,14 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
           D.gr_time_ratio > 0 && (double)(t0 - last_gr_end) > D.gr_time_ratio * (double)last_gr_ns;
     }
     fresh = false;
-    round_phase(D, sh, r, gen, prev_valid, rnd, st);
+    unsigned long long tp = t0;
+    round_phase(D, sh, r, gen, prev_valid, rnd, st, tp);
     if (!grid_sync(D, sh, 4)) return false;
-    if (timer) D.ctl->t_dis += gtimer() - t0;
+    if (timer) {
+      const unsigned long long t3 = gtimer();
+      D.ctl->t_dis += t3 - t0;
+      D.ctl->t_rwait += t3 - tp;
+    }
     since_gr += __ldcg(&D.ctl->work[rnd % 3]);
     time_req = __ldcg(&D.ctl->gr_req[rnd & 1]) != 0;
     r++;
@@ -817,7 +882,10 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
 
 __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
   __shared__ Shared sh;
-  if (threadIdx.x == 0) sh.bars = 0;
+  if (threadIdx.x == 0) {
+    sh.bars = 0;
+    sh.qn = 0;
+  }
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   TStat st;

@@ -40,7 +40,9 @@ class Stats(ctypes.Structure):
                 ("pushes", ctypes.c_int64), ("relabels", ctypes.c_int64), ("visits_discharge", ctypes.c_int64),
                 ("visits_bfs", ctypes.c_int64), ("solve_ms", ctypes.c_double),
                 ("preflow_ms", ctypes.c_double), ("relabel_ms", ctypes.c_double), ("discharge_ms", ctypes.c_double),
-                ("rounds_by_size", ctypes.c_int64 * 4),
+                ("rounds_by_size", ctypes.c_int64 * 4), ("round_work_ms", ctypes.c_double),
+                ("round_tail_ms", ctypes.c_double), ("round_wait_ms", ctypes.c_double),
+                ("level_work_ms", ctypes.c_double), ("level_wait_ms", ctypes.c_double),
                 ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
     def as_dict(self):
@@ -66,7 +68,7 @@ _lib = None
 EXPORTS = ["mf_default_options", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
            "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
            "mf_solve_trace", "mf_destroy_graph", "mf_batch_create", "mf_batch_solve", "mf_batch_get_stats",
-           "mf_batch_destroy"]
+           "mf_batch_destroy", "mf_service_create", "mf_submit", "mf_poll", "mf_wait", "mf_service_destroy"]
 
 
 def lib():
@@ -99,6 +101,12 @@ def lib():
         L.mf_batch_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.mf_batch_destroy.argtypes = [vp]
         L.mf_batch_destroy.restype = None
+        L.mf_service_create.argtypes = [ctypes.c_size_t, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+        L.mf_submit.argtypes = [vp, ctypes.POINTER(GraphDesc), ctypes.POINTER(i64)]
+        L.mf_poll.argtypes = [vp, i64, vp, vp, vp]
+        L.mf_wait.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double)]
+        L.mf_service_destroy.argtypes = [vp]
+        L.mf_service_destroy.restype = None
         _lib = L
     return _lib
 
@@ -329,6 +337,59 @@ class Batch:
     def close(self):
         if self._h:
             lib().mf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Service:
+    """Continuous-batching solver service (mf_service_create / mf_submit / mf_poll / mf_wait)."""
+
+    def __init__(self, budget_bytes: int, options: Options | None = None):
+        self._h = ctypes.c_void_p()
+        self._inst = {}
+        _check(lib().mf_service_create(int(budget_bytes), ctypes.byref(options) if options else None,
+                                       ctypes.byref(self._h)))
+
+    def submit(self, csr: CSR, s: int, t: int) -> int:
+        arr, keep = _descs([csr], [(s, t)])
+        tk = ctypes.c_int64()
+        _check(lib().mf_submit(self._h, arr, ctypes.byref(tk)))
+        self._inst[int(tk.value)] = (csr.n, csr.m)
+        return int(tk.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Latency in ms once the ticket is done, None on timeout."""
+        lat = ctypes.c_double()
+        rc = _check(lib().mf_wait(self._h, ticket, timeout_ms, ctypes.byref(lat)))
+        return None if rc == MF_PENDING else lat.value
+
+    def poll(self, ticket: int, flow=True, cut=True):
+        """Result once ready (the ticket is then forgotten), None while pending."""
+        known = ticket in self._inst
+        n, m = self._inst.get(ticket, (0, 0))
+        v = ctypes.c_int64()
+        f = np.zeros(m, np.int32) if flow and known else None
+        c = np.zeros((n + 31) // 32, np.uint32) if cut and known else None
+        rc = _check(lib().mf_poll(self._h, ticket, ctypes.byref(v), _ptr(f), _ptr(c)))
+        if rc == MF_PENDING:
+            return None
+        self._inst.pop(ticket, None)
+        return Result(int(v.value), f, c)
+
+    def close(self):
+        if self._h:
+            lib().mf_service_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __enter__(self):
