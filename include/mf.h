@@ -251,6 +251,31 @@ int mf_poll(mf_service *svc, mf_ticket ticket, int64_t *flow_value, int32_t *arc
 int mf_wait(mf_service *svc, mf_ticket ticket, int32_t timeout_ms, double *latency_ms);
 void mf_service_destroy(mf_service *svc);
 
+/*
+ * Solve without allocating: for callers that cannot call cudaMalloc (code
+ * running inside another runtime's memory pool or under a fixed memory
+ * budget, plug-ins that must leave the CUDA allocator alone, services that
+ * commit all device memory at start-up). The paper has no counterpart; this is
+ * a deployment variant of mf_solve_device.
+ *
+ * Inputs are device pointers of the current device in the paired-slot format
+ * with int32 offsets: d_row[n + 1], d_head[m], d_cap[m], d_rev[m]; they are
+ * validated as in mf_create_graph. Outputs are device pointers: d_value (one
+ * int64, required), d_flow[m] and d_cut[ceil(n/32)] (nullable). Work is
+ * enqueued on `stream` (a cudaStream_t); the call returns when the solve is
+ * done. All working state lives in one static device scratch area of 32 MiB
+ * that every GPU loading the library holds until the process exits; a graph
+ * needing more (about 48 bytes per vertex + 8 per slot) is rejected with
+ * MF_ERR_TOO_LARGE before any work. The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine. The first call on each device looks
+ * up the scratch area's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture. Every call on a device uses the same scratch
+ * area and re-initialises it; calls whose work overlaps on the GPU race.
+ */
+int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, const int32_t *d_head, const int32_t *d_cap,
+                     const int32_t *d_rev, int32_t s, int32_t t, int64_t *d_value, int32_t *d_flow,
+                     uint32_t *d_cut, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
