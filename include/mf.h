@@ -89,6 +89,10 @@ typedef struct mf_options {
    * a few BFS levels whatever its size, so the work-based trigger alone lets
    * a few trapped vertices climb to n one round at a time. */
   double gr_time_ratio;
+  /* Register budget of the persistent kernel: 0 = up to 128 registers per
+   * thread, 1 = 85 (CTAs of <= 256 threads), 2 = 64 (<= 256 threads),
+   * 3 = 64 (<= 512 threads). Fewer registers keep more warps resident. */
+  int32_t kernel_variant;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a

@@ -217,7 +217,7 @@ int launch_config(mf_graph *g) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
   if (!prop.cooperativeLaunch) return fail(MF_ERR_CUDA, "device %d lacks cooperative launch", g->device);
   int bps = 0;
-  if (solver_occupancy(g->opt.block_threads, &bps) || bps < 1)
+  if (solver_occupancy(g->opt.block_threads, &bps, g->opt.kernel_variant) || bps < 1)
     return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", g->opt.block_threads);
   if (g->opt.blocks_per_sm > 0 && g->opt.blocks_per_sm < bps) bps = g->opt.blocks_per_sm;
   g->grid = bps * prop.multiProcessorCount;
@@ -235,6 +235,11 @@ int check_options(const mf_options *o) {
   if (o->timeout_ms <= 0) return fail(MF_ERR_INVALID_ARG, "timeout_ms must be > 0");
   if (o->max_rounds < 0) return fail(MF_ERR_INVALID_ARG, "max_rounds must be >= 0");
   if (!(o->gr_time_ratio >= 0)) return fail(MF_ERR_INVALID_ARG, "gr_time_ratio must be >= 0");
+  if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
+    return fail(MF_ERR_INVALID_ARG, "kernel_variant must be in [0, %d)", solver_variants());
+  if (o->block_threads > solver_variant_max_threads(o->kernel_variant))
+    return fail(MF_ERR_INVALID_ARG, "kernel_variant %d takes at most %d threads per CTA", o->kernel_variant,
+                solver_variant_max_threads(o->kernel_variant));
   return MF_OK;
 }
 
@@ -276,7 +281,7 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   cudaEventRecord(g->ev0, st);
-  e = launch_solver(D, g->grid, g->block, st);
+  e = launch_solver(D, g->grid, g->block, st, g->opt.kernel_variant);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the solver");
   cudaEventRecord(g->ev1, st);
   e = cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);

@@ -45,6 +45,8 @@ int launch_config(mf_graph *g);
 int check_options(const mf_options *o);
 Dev make_dev(const mf_graph *g);
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
-int solver_occupancy(int block_threads, int *blocks_per_sm);
-cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream);
+int solver_variants();
+int solver_variant_max_threads(int variant);
+int solver_occupancy(int block_threads, int *blocks_per_sm, int variant);
+cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant);
 }  // namespace mf

@@ -180,7 +180,8 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
 
   // launch shape from the device, as for mf_create_graph
   int bps = 0, sms = 0;
-  if (solver_occupancy(o.block_threads, &bps) || bps < 1) return fail(MF_ERR_CUDA, "solver kernel does not fit");
+  if (solver_occupancy(o.block_threads, &bps, o.kernel_variant) || bps < 1)
+    return fail(MF_ERR_CUDA, "solver kernel does not fit");
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device)) != cudaSuccess)
     return cuda_fail(e, "cudaDeviceGetAttribute");
 
@@ -222,7 +223,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   if ((e = cudaMemcpyAsync(term, st_terms, sizeof(st_terms), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "cudaMemcpyAsync");
   if ((e = cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  if ((e = launch_solver(D, bps * sms, o.block_threads, st)) != cudaSuccess)
+  if ((e = launch_solver(D, bps * sms, o.block_threads, st, o.kernel_variant)) != cudaSuccess)
     return cuda_fail(e, "cooperative launch of the solver");
   Ctl c;
   e = cudaMemcpyAsync(&c, D.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);

@@ -164,6 +164,8 @@ struct Shared {
   int flag;
   int qn;                   // staged appends (may exceed QCAP; the excess went straight to the list)
   int qbase;
+  int qk;
+  long long wsum;
   int imin[MAX_WARPS];
   long long lsum[MAX_WARPS];
   int qbuf[QCAP];
@@ -177,6 +179,37 @@ __device__ __forceinline__ void qpush(const Dev &D, Shared &sh, int gen, int val
     sh.qbuf[i] = val;
   else
     append(D, gen, val);
+}
+
+// All threads of the CTA call this at the end of a phase that appended to gen:
+// publishes the staged appends and adds the CTA's sum of `work` to *work_dst
+// (nullable) with two CTA barriers.
+__device__ void phase_end(const Dev &D, Shared &sh, int gen, long long work, long long *work_dst) {
+  const long long w = warp_sum(work);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(reinterpret_cast<unsigned long long *>(&sh.wsum), (unsigned long long)w);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int k = min(sh.qn, QCAP);
+    sh.qk = k;
+    if (k > 0) sh.qbase = atomicAdd(&D.ctl->cnt[gen & 3], k);
+    if (work_dst && sh.wsum) atomic_add64(work_dst, sh.wsum);
+    sh.qn = 0;
+    sh.wsum = 0;
+  }
+  __syncthreads();
+  const int k = sh.qk;
+  if (k > 0) {
+    const int base = sh.qbase;
+    int *L = list_of(D, gen);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const int idx = base + i;
+      if (idx < D.n)
+        L[idx] = sh.qbuf[i];
+      else
+        set_err(D, MF_ERR_INTERNAL, 11);
+    }
+  }
+  // the next phase starts after a grid barrier, which begins with a CTA barrier
 }
 
 // All threads of the CTA call this at the end of a phase that appended to gen.
@@ -295,17 +328,22 @@ __device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_
 // One thread, deg <= KT: arcs cached in registers for all passes.
 __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, int v, int beg, int deg, int dv,
                                  int cap_v, TStat &st, long long &work) {
-  int wv[KT], rs[KT], dw[KT];
+  int wv[KT], rs[KT], dw[KT], rv[KT];
   unsigned act = 0;
-  long long ex = __ldcg(&D.e[v]) + take_added(D, v);
+  // excess: own value plus what neighbours delivered so far; exactly that
+  // delivered amount is taken out of addedExcess at the end (later deliveries stay)
+  const long long got = __ldcg(&D.added[v]);
+  long long ex = __ldcg(&D.e[v]) + got;
 #pragma unroll
   for (int i = 0; i < KT; i++) {
     wv[i] = 0;
     rs[i] = 0;
     dw[i] = 0;
+    rv[i] = 0;
     if (i < deg) {
       wv[i] = __ldg(&D.head[beg + i]);
       rs[i] = __ldcg(&D.rr[beg + i]).x;
+      rv[i] = __ldg(&D.rev[beg + i]);
     }
   }
 #pragma unroll
@@ -318,7 +356,12 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
-  unsigned found = 0;
+  // Discovery test-and-set results are collected per arc and read only after
+  // the discharge, so the atomics of several pushes are in flight together.
+  unsigned tested = 0;
+  int prev_stamp[KT];
+#pragma unroll
+  for (int i = 0; i < KT; i++) prev_stamp[i] = R.r + 1;
   for (;;) {
     int newl = cap_v;
     bool skipped = false;
@@ -332,15 +375,19 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
         } else {
           if (adm) {
             const long long delta = rs[i] < ex ? (long long)rs[i] : ex;
-            push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+            push_res(D, beg + i, rv[i], (int)delta);
             rs[i] -= (int)delta;
             ex -= delta;
             st.pushes++;
             if (dw[i] == 0) {
               to_sink += delta;
               sink = wv[i];
-            } else if (deliver(D, R, wv[i], (act >> i) & 1u, delta)) {
-              found |= 1u << i;
+            } else {
+              atomic_add64((act >> i) & 1u ? &D.added[wv[i]] : &D.e[wv[i]], delta);
+              if (!((tested >> i) & 1u)) {
+                tested |= 1u << i;
+                prev_stamp[i] = atomicExch(act_ptr(D, wv[i], R.p ^ 1), R.r + 1);
+              }
             }
           }
           if (rs[i] > 0 && dw[i] >= dp) newl = min(newl, dw[i] + 1);
@@ -353,10 +400,11 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
     work += deg + D.beta;
     if (dp >= cap_v) break;
   }
+  if (got) atomic_add64(&D.added[v], -got);
   finish_vertex(D, sh, R, v, dp, ex, cap_v);
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if ((found >> i) & 1u) qpush(D, sh, R.next, wv[i]);
+    if (prev_stamp[i] != R.r + 1) qpush(D, sh, R.next, wv[i]);
   flush_sink(D, sink, to_sink);
 }
 
@@ -573,7 +621,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
         if (ad) atomic_add64(&D.e[u], ad);  // the excess of a non-member may receive pushes now
       }
     }
-    for (;;) {  // CTA per vertex
+    for (bool any = __syncthreads_or(cls == 3); any;) {  // CTA per vertex
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
       if (cls == 3) sh.pick = threadIdx.x;
@@ -605,9 +653,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
   }
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const unsigned long long t1 = timer ? gtimer() : 0;
-  qflush(D, sh, R.next);
-  const long long wsum = block_sum(work, sh);
-  if (threadIdx.x == 0 && wsum) atomic_add64(&D.ctl->work[rnd % 3], wsum);
+  phase_end(D, sh, R.next, work, &D.ctl->work[rnd % 3]);
   if (timer) {
     const unsigned long long t2 = gtimer();
     D.ctl->t_rwork += t1 - t_phase0;
@@ -649,9 +695,12 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
   }
 #pragma unroll
   for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(lab_ptr(D, w[i], 0)) : 0;
+  // all CAS first (in flight together), then the appends
+#pragma unroll
+  for (int i = 0; i < KT; i++) lab[i] = (cf[i] > 0 && lab[i] == UNV) ? atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) : 0;
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if (cf[i] > 0 && lab[i] == UNV && atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) == UNV) qpush(D, sh, next, w[i]);
+    if (cf[i] > 0 && lab[i] == UNV) qpush(D, sh, next, w[i]);
 }
 
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
@@ -671,7 +720,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       st.scans_bfs += deg;
       st.visits_bfs++;
     }
-    for (;;) {
+    for (bool any = __syncthreads_or(cls == 3); any;) {
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
       if (cls == 3) sh.pick = v;
@@ -696,7 +745,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
     if (cls == 1) bfs_thread(D, sh, beg, deg, lvl, reverse, next);
     __syncwarp();
   }
-  qflush(D, sh, next);
+  phase_end(D, sh, next, 0, nullptr);
 }
 
 // BFS from `seeds` (label 0) on label slot 0. `blockers` get UNV + 1 and are
@@ -880,11 +929,12 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
 
 // ------------------------------------------------------------------ kernel
 
-__global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
+__device__ __forceinline__ void solve_body(const Dev &D) {
   __shared__ Shared sh;
   if (threadIdx.x == 0) {
     sh.bars = 0;
     sh.qn = 0;
+    sh.wsum = 0;
   }
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -987,17 +1037,44 @@ __global__ void __launch_bounds__(MAX_BLOCK) solve_kernel(Dev D) {
   if (tid == 0) D.ctl->t_end = gtimer();
 }
 
+// Register-budget variants of the same kernel: __launch_bounds__(MAXT, MINB)
+// caps registers at 65536 / (MAXT * MINB) so that more warps stay resident.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) solve_kernel(Dev D) {
+  solve_body(D);
+}
+
 // ------------------------------------------------------------------ host side
 
-int solver_occupancy(int block_threads, int *blocks_per_sm) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block_threads, 0);
+struct Variant {
+  const void *fn;
+  int max_threads;
+};
+
+static const Variant kVariants[] = {
+    {(const void *)solve_kernel<512, 1>, 512},  // up to 128 registers
+    {(const void *)solve_kernel<256, 3>, 256},  // up to 85
+    {(const void *)solve_kernel<256, 4>, 256},  // up to 64
+    {(const void *)solve_kernel<512, 2>, 512},  // up to 64
+};
+constexpr int NUM_VARIANTS = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int solver_variants() { return NUM_VARIANTS; }
+
+int solver_variant_max_threads(int variant) {
+  return variant >= 0 && variant < NUM_VARIANTS ? kVariants[variant].max_threads : 0;
+}
+
+int solver_occupancy(int block_threads, int *blocks_per_sm, int variant) {
+  if (variant < 0 || variant >= NUM_VARIANTS) return -1;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kVariants[variant].fn, block_threads, 0);
   return e == cudaSuccess ? 0 : -1;
 }
 
-cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream) {
+cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant) {
   Dev d = D;
   void *args[] = {&d};
-  return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args, 0, stream);
+  return cudaLaunchCooperativeKernel(kVariants[variant].fn, dim3(grid), dim3(block), args, 0, stream);
 }
 
 }  // namespace mf

@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
     _fields_ = [("gr_freq", ctypes.c_double), ("gr_alpha", ctypes.c_int32), ("work_beta", ctypes.c_int32),
                 ("bin_thread", ctypes.c_int32), ("bin_warp", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int32),
-                ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32), ("gr_time_ratio", ctypes.c_double)]
+                ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32), ("gr_time_ratio", ctypes.c_double),
+                ("kernel_variant", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

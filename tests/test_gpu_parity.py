@@ -84,6 +84,14 @@ def test_degree_bins_agree(gpu, bins):
         solve_and_compare(gpu, g, opt)
 
 
+@pytest.mark.parametrize("variant,bt", [(0, 256), (1, 256), (2, 256), (3, 512), (2, 128)])
+def test_kernel_variants_agree(gpu, variant, bt):
+    """Every register-budget variant of the persistent kernel gives the same unique results."""
+    opt = gpu.default_options(kernel_variant=variant, block_threads=bt)
+    for g in (I.grid3d(18, 20, 10, seed=variant), I.rmat(11, 8, 40 + variant), I.grid2d(40, 60, variant)):
+        solve_and_compare(gpu, g, opt)
+
+
 @pytest.mark.parametrize("bt", [64, 128, 512])
 def test_block_shapes(gpu, bt):
     opt = gpu.default_options(block_threads=bt)
