@@ -198,8 +198,12 @@ int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d
 /* Tracing: solves g like mf_solve (no outputs) and records, for each of the
  * first `capacity` push-relabel rounds of both phases, the working-set size
  * (live[k]) and whether a global relabel ran right before the round
- * (relabel_before[k] = 1). *rounds = total rounds (may exceed capacity). */
-int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds);
+ * (relabel_before[k] = 1), and for each of the first `level_capacity` BFS
+ * levels its frontier size (level_sizes[k]). *rounds and *levels (nullable)
+ * = totals (may exceed the capacities). Host arrays, nullable when their
+ * capacity is 0. */
+int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds,
+                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels);
 
 /* Counters of the last solve on g. */
 int mf_get_stats(const mf_graph *g, mf_stats *out);

@@ -116,8 +116,8 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->e, g->added, g->list[0], g->list[1], g->list[2],
-                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->lab[0], g->lab[1], g->act[0], g->act[1], g->e, g->added,
+                g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -159,7 +159,10 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
   if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
-  if ((rc = dalloc((void **)&g->vs, n * 16, "cudaMalloc vertex state"))) return rc;
+  for (int k = 0; k < 2; k++) {
+    if ((rc = dalloc((void **)&g->lab[k], n * 4, "cudaMalloc labels"))) return rc;
+    if ((rc = dalloc((void **)&g->act[k], n * 4, "cudaMalloc active stamps"))) return rc;
+  }
   if ((rc = dalloc((void **)&g->e, n * 8, "cudaMalloc excess"))) return rc;
   if ((rc = dalloc((void **)&g->added, n * 8, "cudaMalloc addedExcess"))) return rc;
   for (int k = 0; k < 3; k++)
@@ -255,7 +258,10 @@ Dev make_dev(const mf_graph *g) {
   D.rev = g->rev;
   D.cap = g->cap;
   D.rr = g->rr;
-  D.vs = g->vs;
+  for (int k = 0; k < 2; k++) {
+    D.lab[k] = g->lab[k];
+    D.act[k] = g->act[k];
+  }
   D.e = g->e;
   D.added = g->added;
   for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
@@ -501,20 +507,36 @@ int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d
   return solve_into(g, (cudaStream_t)stream, d_flow_value, d_arc_flow, d_cut_bits);
 }
 
-int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds) {
+int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds,
+                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels) {
   clear_error();
-  if (!g || capacity < 0 || (capacity > 0 && (!live || !relabel_before)))
+  if (!g || capacity < 0 || (capacity > 0 && (!live || !relabel_before)) || level_capacity < 0 ||
+      (level_capacity > 0 && !level_sizes))
     return fail(MF_ERR_INVALID_ARG, "bad arguments");
   cudaError_t e = cudaSetDevice(g->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   int2 *tr = nullptr;
+  int *tl = nullptr;
   if (capacity > 0 && (e = cudaMalloc((void **)&tr, (size_t)capacity * sizeof(int2))) != cudaSuccess)
     return cuda_fail(e, "cudaMalloc trace");
+  if (level_capacity > 0 && (e = cudaMalloc((void **)&tl, (size_t)level_capacity * sizeof(int))) != cudaSuccess) {
+    if (tr) cudaFree(tr);
+    return cuda_fail(e, "cudaMalloc trace");
+  }
   Dev D = make_dev(g);
   D.out_value = g->d_value;
   D.trace = tr;
   D.trace_cap = capacity;
+  D.trace_lv = tl;
+  D.trace_lv_cap = level_capacity;
   int rc = run_kernel(g, D, g->stream);
+  if (rc == MF_OK && level_capacity > 0) {
+    const long long nl = g->h_ctl->levels < level_capacity ? g->h_ctl->levels : level_capacity;
+    e = cudaMemcpy(level_sizes, tl, (size_t)nl * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "trace copy");
+  }
+  if (levels && rc == MF_OK) *levels = g->h_ctl->levels;
+  if (tl) cudaFree(tl);
   if (rc == MF_OK && capacity > 0) {
     const long long nr = g->h_ctl->rounds < capacity ? g->h_ctl->rounds : capacity;
     int2 *h = (int2 *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int2));
@@ -567,13 +589,11 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }
   if (label) {
-    int4 *tmp = (int4 *)malloc(n * sizeof(int4));
-    if (!tmp) return fail(MF_ERR_OOM, "host allocation");
-    e = cudaMemcpyAsync(tmp, g->vs, n * sizeof(int4), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaMemcpyAsync(label, g->lab[0], n * sizeof(int), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    for (size_t v = 0; v < n && e == cudaSuccess; v++) label[v] = tmp[v].x > g->n ? g->n : tmp[v].x;
-    free(tmp);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
+    for (size_t v = 0; v < n; v++)
+      if (label[v] > g->n) label[v] = g->n;
   }
   if (excess) {
     e = cudaMemcpyAsync(excess, g->e, n * 8, cudaMemcpyDeviceToHost, g->stream);

@@ -39,11 +39,12 @@ struct Ctl {
 
 // Device view of one (possibly multi-instance) graph.
 //
-// Vertex state vs[v] = {label slot 0, label slot 1, active stamp slot 0,
-// active stamp slot 1} (one 16-byte gather per arc). Round r reads the label
-// of every vertex from slot r & 1 and a discharged vertex writes d' into slot
-// (r + 1) & 1; a vertex is in the working set of round r iff its stamp in slot
-// r & 1 equals r. Slot 0 holds the labels during a BFS and at phase ends.
+// Vertex state: labels lab[0..1][v] and active-round stamps act[0..1][v], four
+// dense int32 arrays (eight vertices per 32-byte sector, 4n bytes each, small
+// enough to stay in L2). Round r reads the label of every vertex from slot
+// r & 1 and a discharged vertex writes d' into slot (r + 1) & 1; a vertex is in
+// the working set of round r iff act[r & 1][v] == r. Slot 0 holds the labels
+// during a BFS and at phase ends.
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
@@ -54,7 +55,8 @@ struct Dev {
   const int *__restrict__ rev;   // m
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
-  int4 *vs;          // n: vertex state (above)
+  int *lab[2];       // n each: label slots (above)
+  int *act[2];       // n each: active-round stamp slots (above)
   long long *e;      // n: excess
   long long *added;  // n: excess received while the vertex is in the working set
   int *list[3];      // vertex lists, generation g uses list[g % 3]
@@ -77,6 +79,8 @@ struct Dev {
   // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
   int2 *trace;
   long long trace_cap;
+  int *trace_lv;          // nullable: frontier size of every BFS level, in order
+  long long trace_lv_cap;
   // outputs (device pointers, each nullable)
   long long *out_value;   // per instance
   int *out_flow;          // m

@@ -15,7 +15,7 @@
 // Data model (mf_device.cuh): CSR of paired slots with an inline copy of the
 // reverse residual (int2 rr[a] = {res[a], res[rev[a]]}, the "each edge also
 // stores the residual capacity of its reverse edge" layout of Section 4.2),
-// per-vertex int4 vs[v] = {label slots, active-round stamps}, int64 excess.
+// per-vertex int32 label and active-stamp slots, int64 excess.
 // Vertex lists are plain arrays filled by warp-aggregated atomics; a list is
 // consumed in tiles of blockDim entries that are binned in shared memory by
 // degree (thread / warp / CTA per vertex).
@@ -77,12 +77,8 @@ __device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigne
 __device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
 
 // label slot p / active stamp slot p of v
-__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return reinterpret_cast<int *>(&D.vs[v]) + p; }
-__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) {
-  return reinterpret_cast<int *>(&D.vs[v]) + 2 + p;
-}
-__device__ __forceinline__ int lab_of(const int4 &x, int p) { return p ? x.y : x.x; }
-__device__ __forceinline__ int act_of(const int4 &x, int p) { return p ? x.w : x.z; }
+__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return D.lab[p] + v; }
+__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return D.act[p] + v; }
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
@@ -346,12 +342,12 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
       rv[i] = __ldg(&D.rev[beg + i]);
     }
   }
+  const int *labp = D.lab[R.p], *actp = D.act[R.p];
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (rs[i] > 0) {
-      const int4 x = __ldcg(&D.vs[wv[i]]);
-      dw[i] = lab_of(x, R.p);
-      if (act_of(x, R.p) == R.r) act |= 1u << i;
+      dw[i] = __ldcg(labp + wv[i]);
+      if (__ldcg(actp + wv[i]) == R.r) act |= 1u << i;
     }
   int dp = dv;
   long long to_sink = 0;
@@ -431,9 +427,8 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          const int4 x = __ldcg(&D.vs[w]);
-          dw = lab_of(x, R.p);
-          wact = act_of(x, R.p) == R.r;
+          dw = __ldcg(lab_ptr(D, w, R.p));
+          wact = __ldcg(act_ptr(D, w, R.p)) == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -503,9 +498,8 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          const int4 x = __ldcg(&D.vs[w]);
-          dw = lab_of(x, R.p);
-          wact = act_of(x, R.p) == R.r;
+          dw = __ldcg(lab_ptr(D, w, R.p));
+          wact = __ldcg(act_ptr(D, w, R.p)) == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -614,9 +608,8 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       }
     } else if (idx < total) {
       const int u = __ldcg(&P[idx - count]);
-      const int4 x = __ldcg(&D.vs[u]);
-      if (act_of(x, R.p) != r) {  // not in this working set
-        *lab_ptr(D, u, R.p ^ 1) = lab_of(x, R.p);
+      if (__ldcg(act_ptr(D, u, R.p)) != r) {  // not in this working set
+        *lab_ptr(D, u, R.p ^ 1) = __ldcg(lab_ptr(D, u, R.p));
         const long long ad = take_added(D, u);
         if (ad) atomic_add64(&D.e[u], ad);  // the excess of a non-member may receive pushes now
       }
@@ -782,7 +775,12 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   for (int lvl = 0;; lvl++) {
-    if (list_count(D, gen) == 0) break;
+    const int fcount = list_count(D, gen);
+    if (fcount == 0) break;
+    if (timer && D.trace_lv) {
+      const long long k = D.ctl->levels;
+      if (k < D.trace_lv_cap) D.trace_lv[k] = fcount;
+    }
     const unsigned long long t0 = timer ? gtimer() : 0;
     bfs_level(D, sh, gen, lvl, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
@@ -816,7 +814,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     const int x = __ldcg(lab_ptr(D, v, 0));
     const int c = cap_of(D, v);
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
-    *reinterpret_cast<int2 *>(&D.vs[v]) = make_int2(d, d);
+    if (d != x) D.lab[0][v] = d;
+    D.lab[1][v] = d;
     long long ev = __ldcg(&D.e[v]);
     const long long ad = __ldcg(&D.added[v]);
     if (ad) {
@@ -841,7 +840,7 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   for (int v = tid; v < D.n; v += nthr) {
     const int d = __ldcg(lab_ptr(D, v, p));
-    *reinterpret_cast<int2 *>(&D.vs[v]) = make_int2(d, d);
+    D.lab[p ^ 1][v] = d;
     const long long ad = __ldcg(&D.added[v]);
     if (ad) {
       D.e[v] = __ldcg(&D.e[v]) + ad;
@@ -945,7 +944,10 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   // excess 0, no stamps.
   for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
   for (int v = tid; v < D.n; v += nthr) {
-    D.vs[v] = make_int4(0, 0, -1, -1);
+    D.lab[0][v] = 0;
+    D.lab[1][v] = 0;
+    D.act[0][v] = -1;
+    D.act[1][v] = -1;
     D.e[v] = 0;
     D.added[v] = 0;
   }

@@ -94,7 +94,7 @@ def lib():
         L.mf_solve_device.argtypes = [vp, vp, vp, vp, vp]
         L.mf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.mf_run_rounds.argtypes = [vp, i64, i32, vp, vp, vp, vp]
-        L.mf_solve_trace.argtypes = [vp, vp, vp, i64, vp]
+        L.mf_solve_trace.argtypes = [vp, vp, vp, i64, vp, vp, i64, vp]
         L.mf_destroy_graph.argtypes = [vp]
         L.mf_destroy_graph.restype = None
         L.mf_batch_create.argtypes = [i32, vp, ctypes.POINTER(Options), ctypes.POINTER(vp)]
@@ -238,14 +238,17 @@ class Graph:
         """Outputs into torch CUDA tensors (int64[1], int32[m], int32/uint32[ceil(n/32)]), each optional."""
         _check(lib().mf_solve_device(self._h, _stream_ptr(stream), _ptr(value), _ptr(flow), _ptr(cut_bits)))
 
-    def solve_trace(self, capacity: int = 1 << 22):
-        """Per-round working-set sizes and relabel markers of one solve: (live int32[k], relabel int32[k])."""
+    def solve_trace(self, capacity: int = 1 << 22, level_capacity: int = 1 << 22):
+        """One traced solve: (live int32[rounds], relabel int32[rounds], bfs frontier sizes int32[levels])."""
         live = np.zeros(capacity, np.int32)
         gr = np.zeros(capacity, np.int32)
-        nr = ctypes.c_int64()
-        _check(lib().mf_solve_trace(self._h, _ptr(live), _ptr(gr), capacity, ctypes.byref(nr)))
+        lv = np.zeros(level_capacity, np.int32)
+        nr, nl = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mf_solve_trace(self._h, _ptr(live), _ptr(gr), capacity, ctypes.byref(nr), _ptr(lv),
+                                    level_capacity, ctypes.byref(nl)))
         k = min(int(nr.value), capacity)
-        return live[:k], gr[:k]
+        kl = min(int(nl.value), level_capacity)
+        return live[:k], gr[:k], lv[:kl]
 
     def stats(self) -> dict:
         s = Stats()

@@ -253,3 +253,16 @@ def test_round_limit_reports_error(gpu):
         # the graph stays usable after an error
     with gpu.Graph.from_csr(csr, g.s, g.t) as G:
         assert G.solve().value == oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap)["value"]
+
+
+def test_trace_matches_stats(gpu):
+    """mf_solve_trace: one entry per round and per BFS level, consistent with the solve's counters."""
+    g = I.grid3d(30, 30, 16, seed=9)
+    csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
+    with gpu.Graph.from_csr(csr, g.s, g.t) as G:
+        live, gr, levels = G.solve_trace()
+        st = G.stats()
+    assert len(live) == st["rounds"] and len(levels) == st["bfs_levels"]
+    assert gr[0] == 1 and int(gr.sum()) <= st["global_relabels"]
+    assert (live > 0).all()
+    assert int(levels.sum()) == st["visits_bfs"]
