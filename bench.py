@@ -121,6 +121,15 @@ def load_workload(shape=None):
     return g, csr
 
 
+def kernel_source_hash() -> str:
+    """Identifies the solver kernel version the stored ncu counters belong to."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_1507_01926_gb300", "csrc")
+    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("mf_solver.cu", "mf_device.cuh"))
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
 def golden_value():
     p = os.path.join(ROOT, "tests", "golden", "config1.json")
     if os.path.exists(p):
@@ -398,8 +407,10 @@ def main():
     achieved = (sum(mb) / len(mb)) / (statistics.mean(per_step) / 1000.0) / 1e9
     traffic = None
     tp = os.path.join(ROOT, "profiles", "solve_kernel_grid3d_256x256x128.json")
-    if os.path.exists(tp):
-        traffic = json.load(open(tp)).get("dram_bytes_per_launch")
+    if os.path.exists(tp) and tuple(args.grid3d) == (256, 256, 128):
+        rec = json.load(open(tp))
+        if rec.get("kernel_source_sha256_16") == kernel_source_hash():
+            traffic = rec.get("dram_bytes_per_launch")  # counters of this very kernel version
 
     if rank != 0:
         G.close()
