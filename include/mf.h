@@ -93,6 +93,13 @@ typedef struct mf_options {
    * thread, 1 = 85 (CTAs of <= 256 threads), 2 = 64 (<= 256 threads),
    * 3 = 64 (<= 512 threads). Fewer registers keep more warps resident. */
   int32_t kernel_variant;
+  /* 1: run the simple synchronous rounds of Section 3 instead of the improved
+   * discharge of Section 3.1: each round pushes along admissible arcs with the
+   * round-start labels, then relabels every vertex still holding excess once.
+   * No arc is contested and nothing is read while it changes, so with
+   * gr_time_ratio = 0 (forced in this mode) every solve of a graph gives the
+   * same per-arc flow. More rounds than the default. */
+  int32_t simple_rounds;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a

@@ -275,7 +275,8 @@ Dev make_dev(const mf_graph *g) {
   const double thr = ((double)g->opt.gr_alpha * (double)g->n_total_for_gr + (double)g->m_arcs) / g->opt.gr_freq;
   D.gr_threshold = thr > 9.0e18 ? (long long)9e18 : (long long)thr;
   D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
-  D.gr_time_ratio = g->opt.gr_time_ratio;
+  D.simple = g->opt.simple_rounds ? 1 : 0;
+  D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
   D.cut_only = g->opt.cut_only;

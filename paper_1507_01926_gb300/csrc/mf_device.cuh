@@ -76,6 +76,7 @@ struct Dev {
   long long stop_rounds;
   int final_gr;
   int cut_only;
+  int simple;              // 1: the simple synchronous rounds of Section 3 (push pass, then one relabel)
   // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
   int2 *trace;
   long long trace_cap;

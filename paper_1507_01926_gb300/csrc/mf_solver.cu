@@ -244,15 +244,16 @@ __device__ long long block_sum(long long x, Shared &sh) {
 }
 
 // Grid barrier on a monotone 64-bit arrival counter: CTA k's b-th arrival is
-// complete when the counter reaches b * gridDim.x. Every wait is bounded by
-// D.timeout_ns; on expiry the error word is set and all CTAs leave at their
-// next barrier.
+// complete when the counter reaches b * gridDim.x. The CTA barrier orders the
+// CTA's writes before thread 0's release add, and thread 0's acquire load
+// before the CTA barrier that releases the other threads. Every wait is
+// bounded by D.timeout_ns; on expiry the error word is set and all CTAs leave
+// at their next barrier.
 __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long *c = reinterpret_cast<unsigned long long *>(&D.ctl->bar);
     const unsigned long long target = (sh.bars + 1) * (unsigned long long)gridDim.x;
-    __threadfence();
     red_release_add64(c, 1ULL);
     if (ld_acquire64(c) < target) {
       const unsigned long long t0 = gtimer();
@@ -266,7 +267,6 @@ __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
       }
     }
     sh.bars++;
-    __threadfence();
   }
   __syncthreads();
   return vol_read(&D.ctl->err) == 0;
@@ -328,7 +328,8 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
   unsigned act = 0;
   // excess: own value plus what neighbours delivered so far; exactly that
   // delivered amount is taken out of addedExcess at the end (later deliveries stay)
-  const long long got = __ldcg(&D.added[v]);
+  // (simple rounds: only the round-start excess; deliveries are folded in after the pushes)
+  const long long got = D.simple ? 0 : __ldcg(&D.added[v]);
   long long ex = __ldcg(&D.e[v]) + got;
 #pragma unroll
   for (int i = 0; i < KT; i++) {
@@ -366,7 +367,7 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
       if (i < deg && ex > 0 && rs[i] > 0) {
         st.scans_dis++;
         const bool adm = (dp == dw[i] + 1);
-        if (adm && ((act >> i) & 1u) && !wins(dv, dw[i], v, wv[i])) {
+        if (adm && !D.simple && ((act >> i) & 1u) && !wins(dv, dw[i], v, wv[i])) {
           skipped = true;
         } else {
           if (adm) {
@@ -390,14 +391,17 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
         }
       }
     }
-    if (ex == 0 || skipped) break;
+    if (ex == 0 || skipped || D.simple) break;
     dp = newl;
     st.relabels++;
     work += deg + D.beta;
     if (dp >= cap_v) break;
   }
   if (got) atomic_add64(&D.added[v], -got);
-  finish_vertex(D, sh, R, v, dp, ex, cap_v);
+  if (D.simple)
+    D.e[v] = ex;  // label and re-activation: relabel_phase
+  else
+    finish_vertex(D, sh, R, v, dp, ex, cap_v);
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (prev_stamp[i] != R.r + 1) qpush(D, sh, R.next, wv[i]);
@@ -411,7 +415,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
   long long ex = 0;
-  if (lane == 0) ex = __ldcg(&D.e[v]) + take_added(D, v);
+  if (lane == 0) ex = __ldcg(&D.e[v]) + (D.simple ? 0 : take_added(D, v));
   ex = __shfl_sync(FULL, ex, 0);
   int dp = dv;
   long long to_sink = 0;
@@ -433,7 +437,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
       }
       const bool resid = rs > 0;
       const bool adm = resid && dp == dw + 1;
-      const bool skip = adm && wact && !wins(dv, dw, v, w);
+      const bool skip = adm && !D.simple && wact && !wins(dv, dw, v, w);
       const bool pushable = adm && !skip;
       const long long pr = pushable ? (long long)rs : 0;
       const long long incl = warp_incl_scan(pr, lane);
@@ -460,7 +464,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
       ex = total >= ex ? 0 : ex - total;
     }
     newl = warp_min(newl);
-    if (ex == 0 || skipped) break;
+    if (ex == 0 || skipped || D.simple) break;
     dp = newl;
     if (lane == 0) {
       st.relabels++;
@@ -468,7 +472,12 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
     }
     if (dp >= cap_v) break;
   }
-  if (lane == 0) finish_vertex(D, sh, R, v, dp, ex, cap_v);
+  if (lane == 0) {
+    if (D.simple)
+      D.e[v] = ex;
+    else
+      finish_vertex(D, sh, R, v, dp, ex, cap_v);
+  }
   __syncwarp();
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncwarp();
@@ -481,7 +490,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
   __syncthreads();
-  if (threadIdx.x == 0) sh.lsum[0] = __ldcg(&D.e[v]) + take_added(D, v);
+  if (threadIdx.x == 0) sh.lsum[0] = __ldcg(&D.e[v]) + (D.simple ? 0 : take_added(D, v));
   __syncthreads();
   long long ex = sh.lsum[0];
   int dp = dv;
@@ -504,7 +513,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
       }
       const bool resid = rs > 0;
       const bool adm = resid && dp == dw + 1;
-      const bool skip = adm && wact && !wins(dv, dw, v, w);
+      const bool skip = adm && !D.simple && wact && !wins(dv, dw, v, w);
       const bool pushable = adm && !skip;
       const long long pr = pushable ? (long long)rs : 0;
       const long long incl_w = warp_incl_scan(pr, lane);
@@ -548,7 +557,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
     __syncthreads();
     newl = cap_v;
     for (int k = 0; k < nw; k++) newl = min(newl, sh.imin[k]);
-    if (ex == 0 || skipped) break;
+    if (ex == 0 || skipped || D.simple) break;
     dp = newl;
     if (threadIdx.x == 0) {
       st.relabels++;
@@ -556,7 +565,12 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
     }
     if (dp >= cap_v) break;
   }
-  if (threadIdx.x == 0) finish_vertex(D, sh, R, v, dp, ex, cap_v);
+  if (threadIdx.x == 0) {
+    if (D.simple)
+      D.e[v] = ex;
+    else
+      finish_vertex(D, sh, R, v, dp, ex, cap_v);
+  }
   if (sink >= 0) flush_sink(D, sink, to_sink);
   __syncthreads();
 }
@@ -653,6 +667,97 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
     D.ctl->t_rtail += t2 - t1;
     t_phase0 = t2;
   }
+}
+
+// Simple synchronous rounds (Section 3, steps 2-3): after all pushes of the
+// round, every vertex of the working set still holding excess relabels once,
+// d := 1 + min{d(w) : (v,w) residual} with the round-start labels, capped at
+// n; the new label goes to the next slot and the vertex re-enters the working
+// set when it is below n. Vertices without excess keep their label.
+__device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd, TStat &st) {
+  const RoundCtx R{r, r & 1, gen + 1};
+  const int *W = list_of(D, gen);
+  const int count = list_count(D, gen);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int *labp = D.lab[R.p];
+  long long work = 0;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+    const int idx = base + threadIdx.x;
+    int v = -1, beg = 0, deg = 0, cls = 0, cap_v = 0;
+    if (idx < count) {
+      v = __ldcg(&W[idx]);
+      const int dv = __ldcg(lab_ptr(D, v, R.p));
+      cap_v = cap_of(D, v);
+      // Section 3 step 4 for this vertex: the excess it received this round joins its excess now
+      const long long ex_own = __ldcg(&D.e[v]);
+      const long long ad = dv >= cap_v ? 0 : take_added(D, v);
+      if (ad) D.e[v] = ex_own + ad;
+      if (dv >= cap_v) {
+        v = -1;  // retired in the push step
+      } else if (ex_own == 0) {
+        *lab_ptr(D, v, R.p ^ 1) = dv;
+        v = -1;
+      } else {
+        beg = __ldg(&D.row[v]);
+        deg = __ldg(&D.row[v + 1]) - beg;
+        cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
+      }
+    }
+    int newl = INT_MAX;
+    for (bool any = __syncthreads_or(cls == 3); any;) {  // CTA per vertex
+      if (threadIdx.x == 0) sh.pick = -1;
+      __syncthreads();
+      if (cls == 3) sh.pick = threadIdx.x;
+      __syncthreads();
+      const int pt = sh.pick;
+      if (pt < 0) break;
+      if (threadIdx.x == pt) {
+        cls = 0;
+        sh.imin[0] = v;
+      }
+      __syncthreads();
+      const int bv = sh.imin[0];
+      const int b = __ldg(&D.row[bv]), e = __ldg(&D.row[bv + 1]);
+      int m = INT_MAX;
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x)
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(labp + __ldg(&D.head[a])) + 1);
+      m = warp_min(m);
+      __syncthreads();
+      if (lane == 0) sh.imin[wid] = m;
+      __syncthreads();
+      if (threadIdx.x == pt)
+        for (int k = 0; k < nw; k++) newl = min(newl, sh.imin[k]);
+      __syncthreads();
+    }
+    for (;;) {  // warp per vertex
+      const unsigned mm = __ballot_sync(FULL, cls == 2);
+      if (!mm) break;
+      const int leader = __ffs(mm) - 1;
+      const int pv = __shfl_sync(FULL, v, leader);
+      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      int m = INT_MAX;
+      for (int a = b + lane; a < e; a += 32)
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(labp + __ldg(&D.head[a])) + 1);
+      m = warp_min(m);
+      if (lane == leader) {
+        cls = 0;
+        newl = m;
+      }
+    }
+    if (cls == 1) {
+      for (int a = beg; a < beg + deg; a++)
+        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(labp + __ldg(&D.head[a])) + 1);
+    }
+    if (v >= 0) {
+      newl = min(newl, cap_v);
+      *lab_ptr(D, v, R.p ^ 1) = newl;
+      st.relabels++;
+      work += deg + D.beta;
+      if (newl < cap_v && atomicExch(act_ptr(D, v, R.p ^ 1), r + 1) != r + 1) qpush(D, sh, R.next, v);
+    }
+    __syncwarp();
+  }
+  phase_end(D, sh, R.next, work, &D.ctl->work[rnd % 3]);
 }
 
 // ------------------------------------------------------------------ BFS
@@ -897,6 +1002,10 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     unsigned long long tp = t0;
     round_phase(D, sh, r, gen, prev_valid, rnd, st, tp);
     if (!grid_sync(D, sh, 4)) return false;
+    if (D.simple) {
+      relabel_phase(D, sh, r, gen, rnd, st);
+      if (!grid_sync(D, sh, 4)) return false;
+    }
     if (timer) {
       const unsigned long long t3 = gtimer();
       D.ctl->t_dis += t3 - t0;

@@ -266,3 +266,29 @@ def test_trace_matches_stats(gpu):
     assert gr[0] == 1 and int(gr.sum()) <= st["global_relabels"]
     assert (live > 0).all()
     assert int(levels.sum()) == st["visits_bfs"]
+
+
+@pytest.mark.parametrize("which", ["grid2d", "grid3d", "rmat", "layered", "random", "hub"])
+def test_simple_rounds_parity(gpu, which):
+    """The simple synchronous rounds of Section 3 (one push pass, then at most one relabel per round)."""
+    g = {"grid2d": I.grid2d(60, 80, 1), "grid3d": I.grid3d(24, 20, 12, seed=2), "rmat": I.rmat(12, 8, 3),
+         "layered": I.layered(20, 120, 4), "random": I.random_graph(200, 1600, 5, cap=(0, 300)),
+         "hub": I.random_graph(15, 4000, 6, cap=(1, 80))}[which]
+    solve_and_compare(gpu, g, gpu.default_options(simple_rounds=1))
+
+
+def test_simple_rounds_are_deterministic(gpu):
+    """Without contested arcs or read races, repeated solves give the same per-arc flow (and the same
+    number of rounds), on the same graph object and on a fresh one."""
+    g = I.grid3d(28, 24, 14, seed=11)
+    csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
+    opt = gpu.default_options(simple_rounds=1)
+    runs = []
+    for _ in range(2):
+        with gpu.Graph.from_csr(csr, g.s, g.t, opt) as G:
+            for _ in range(2):
+                r = G.solve()
+                runs.append((r.value, r.flow.copy(), r.cut_bits.copy(), G.stats()["rounds"]))
+    for v, f, c, k in runs[1:]:
+        assert v == runs[0][0] and k == runs[0][3]
+        assert np.array_equal(f, runs[0][1]) and np.array_equal(c, runs[0][2])
