@@ -154,6 +154,20 @@ def cpu_baseline(g, seconds: float = 12.0):
             "seconds": r["seconds"], "scans": done}
 
 
+def aggregate_ranks(total_ms: float, scans: float, device):
+    """Whole-job figures over the ranks of the process group: the slowest rank's timed milliseconds and the
+    arc scans of all ranks (replicas: every rank solves its own copy)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(total_ms), float(scans)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -389,12 +403,7 @@ def main():
     total_ms = sum(per_step)
     scans = sum(s["scans_discharge"] + s["scans_bfs"] for s in stats)
     if world > 1:
-        t = torch.tensor([total_ms, float(scans)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        total_ms_max, scans_all = float(mx[0]), float(sm[1])
+        total_ms_max, scans_all = aggregate_ranks(total_ms, scans, dev)
     else:
         total_ms_max, scans_all = total_ms, float(scans)
     value = scans_all / (total_ms_max / 1000.0)

@@ -292,3 +292,23 @@ def test_simple_rounds_are_deterministic(gpu):
     for v, f, c, k in runs[1:]:
         assert v == runs[0][0] and k == runs[0][3]
         assert np.array_equal(f, runs[0][1]) and np.array_equal(c, runs[0][2])
+
+
+def test_device_wait_timeout_reported_and_graph_reusable(gpu):
+    """Failure detection without a fault: with a 1 ms limit on device-side waits, a solve whose single
+    CTA-wide discharge of a 4-million-arc hub takes far longer than that makes the other CTAs' barrier
+    waits run out; the solve returns MF_ERR_TIMEOUT and the same graph then solves normally."""
+    k = 1 << 22
+    hub, t = 1, k + 2
+    tail = np.concatenate([[0], np.full(k, hub), np.arange(2, k + 2)]).astype(np.int32)
+    head = np.concatenate([[hub], np.arange(2, k + 2), np.full(k, t)]).astype(np.int32)
+    cap = np.ones(2 * k + 1, np.int32)
+    cap[0] = k
+    g = I.Instance(k + 3, 0, t, tail, head, cap, "hub")
+    csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
+    with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(timeout_ms=1)) as G:
+        with pytest.raises(gpu.MFError) as e:
+            G.solve(flow=False, cut=False)
+        assert e.value.code == -8
+    with gpu.Graph.from_csr(csr, g.s, g.t) as G:
+        assert G.solve(flow=False, cut=False).value == k

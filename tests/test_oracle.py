@@ -6,7 +6,9 @@
 * closed forms: a path, k disjoint paths, uniform-column 2D and 3D grids, bipartite matching (checked
   against scipy's Hopcroft-Karp),
 * the flow definitions (capacity bounds, conservation, no residual s-t path, cut capacity = value),
-* exact BFS distances (scipy's breadth-first shortest paths) for the global-relabel labels.
+* exact BFS distances (scipy's breadth-first shortest paths) for the global-relabel labels,
+* independent library max-flow implementations (scipy.sparse.csgraph.maximum_flow, networkx) on larger
+  graphs.
 """
 import numpy as np
 import pytest
@@ -233,3 +235,31 @@ def test_checker_catches_planted_mistakes():
     assert oracle.check_flow(g.n, g.s, g.t, g.tail, g.head, g.cap, f, r["value"] + 1, r["cut"])
     cut = r["cut"].copy(); cut[np.nonzero(~cut)[0][0]] = True  # noqa: E702
     assert oracle.check_flow(g.n, g.s, g.t, g.tail, g.head, g.cap, f, r["value"], cut)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_scipy_maximum_flow(seed):
+    """scipy.sparse.csgraph.maximum_flow (an independent library implementation) agrees on the value."""
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(200, 2000))
+    g = I.random_graph(n, int(rng.integers(2 * n, 8 * n)), 300 + seed, cap=(1, int(rng.integers(2, 5000))))
+    r = run_all(g.n, g.s, g.t, g.tail, g.head, g.cap)
+    A = sp.csr_matrix((g.cap.astype(np.int32), (g.tail, g.head)), shape=(g.n, g.n))  # parallel arcs summed
+    A.sum_duplicates()
+    assert r["value"] == int(csgraph.maximum_flow(A, g.s, g.t).flow_value)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_networkx_maximum_flow(seed):
+    nx = pytest.importorskip("networkx")
+    g = I.grid2d(12 + seed, 15, 400 + seed)
+    G = nx.DiGraph()
+    for u, v, c in zip(g.tail.tolist(), g.head.tolist(), g.cap.tolist()):
+        if G.has_edge(u, v):
+            G[u][v]["capacity"] += c
+        else:
+            G.add_edge(u, v, capacity=c)
+    r = run_all(g.n, g.s, g.t, g.tail, g.head, g.cap)
+    assert r["value"] == nx.maximum_flow_value(G, g.s, g.t)
