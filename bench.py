@@ -231,7 +231,7 @@ def run_batch(args):
     prep_s = time.perf_counter() - t0
     nv, ns = sum(c.n for c in csrs), sum(c.m for c in csrs)
     # plain: one launch per instance, graphs already resident
-    k = min(args.plain_count, len(insts))
+    k = min(args.plain_count, len(csrs))
     graphs = [mf.Graph.from_csr(c, s, t) for c, (s, t) in zip(csrs[:k], sts[:k])]
     for G in graphs[: min(3, k)]:
         G.solve(flow=False, cut=False)

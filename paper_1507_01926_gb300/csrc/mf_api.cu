@@ -116,7 +116,7 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->lab[0], g->lab[1], g->act[0], g->act[1], g->e, g->added,
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vst[0], g->vst[1], g->e, g->added,
                 g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -159,10 +159,8 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
   if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
-  for (int k = 0; k < 2; k++) {
-    if ((rc = dalloc((void **)&g->lab[k], n * 4, "cudaMalloc labels"))) return rc;
-    if ((rc = dalloc((void **)&g->act[k], n * 4, "cudaMalloc active stamps"))) return rc;
-  }
+  for (int k = 0; k < 2; k++)
+    if ((rc = dalloc((void **)&g->vst[k], n * 8, "cudaMalloc vertex state"))) return rc;
   if ((rc = dalloc((void **)&g->e, n * 8, "cudaMalloc excess"))) return rc;
   if ((rc = dalloc((void **)&g->added, n * 8, "cudaMalloc addedExcess"))) return rc;
   for (int k = 0; k < 3; k++)
@@ -258,10 +256,7 @@ Dev make_dev(const mf_graph *g) {
   D.rev = g->rev;
   D.cap = g->cap;
   D.rr = g->rr;
-  for (int k = 0; k < 2; k++) {
-    D.lab[k] = g->lab[k];
-    D.act[k] = g->act[k];
-  }
+  for (int k = 0; k < 2; k++) D.vst[k] = g->vst[k];
   D.e = g->e;
   D.added = g->added;
   for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
@@ -590,7 +585,8 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }
   if (label) {
-    e = cudaMemcpyAsync(label, g->lab[0], n * sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaMemcpy2DAsync(label, sizeof(int), g->vst[0], sizeof(int2), sizeof(int), n, cudaMemcpyDeviceToHost,
+                          g->stream);  // the label half of every slot-0 entry
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
     for (size_t v = 0; v < n; v++)

@@ -39,12 +39,12 @@ struct Ctl {
 
 // Device view of one (possibly multi-instance) graph.
 //
-// Vertex state: labels lab[0..1][v] and active-round stamps act[0..1][v], four
-// dense int32 arrays (eight vertices per 32-byte sector, 4n bytes each, small
-// enough to stay in L2). Round r reads the label of every vertex from slot
-// r & 1 and a discharged vertex writes d' into slot (r + 1) & 1; a vertex is in
-// the working set of round r iff act[r & 1][v] == r. Slot 0 holds the labels
-// during a BFS and at phase ends.
+// Vertex state: two slots by round parity, vst[p][v] = {label, active-round
+// stamp} (one 8-byte gather gives both, four vertices per 32-byte sector).
+// Round r reads the label of every vertex from slot r & 1 and a discharged
+// vertex writes d' into slot (r + 1) & 1; a vertex is in the working set of
+// round r iff vst[r & 1][v].y == r. Slot 0 holds the labels during a BFS and
+// at phase ends.
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
@@ -55,8 +55,7 @@ struct Dev {
   const int *__restrict__ rev;   // m
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
-  int *lab[2];       // n each: label slots (above)
-  int *act[2];       // n each: active-round stamp slots (above)
+  int2 *vst[2];      // n each: {label, active-round stamp} slots (above)
   long long *e;      // n: excess
   long long *added;  // n: excess received while the vertex is in the working set
   int *list[3];      // vertex lists, generation g uses list[g % 3]

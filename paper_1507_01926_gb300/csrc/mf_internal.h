@@ -20,8 +20,7 @@ struct mf_graph {
   // device state
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
   int2 *rr = nullptr;
-  int *lab[2] = {nullptr, nullptr};
-  int *act[2] = {nullptr, nullptr};
+  int2 *vst[2] = {nullptr, nullptr};
   long long *e = nullptr, *added = nullptr;
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;

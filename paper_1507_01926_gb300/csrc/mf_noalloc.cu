@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for n vertices and m slots (offsets from the start).
 struct Layout {
-  size_t ctl, flags, term, rr, lab0, lab1, act0, act1, e, added, list0, list1, list2, total;
+  size_t ctl, flags, term, rr, vst0, vst1, e, added, list0, list1, list2, total;
 };
 
 Layout layout(long long n, long long m) {
@@ -52,14 +52,10 @@ Layout layout(long long n, long long m) {
   o = align256(o + 8);
   L.rr = o;
   o = align256(o + 8 * (size_t)m);
-  L.lab0 = o;
-  o = align256(o + 4 * (size_t)n);
-  L.lab1 = o;
-  o = align256(o + 4 * (size_t)n);
-  L.act0 = o;
-  o = align256(o + 4 * (size_t)n);
-  L.act1 = o;
-  o = align256(o + 4 * (size_t)n);
+  L.vst0 = o;
+  o = align256(o + 8 * (size_t)n);
+  L.vst1 = o;
+  o = align256(o + 8 * (size_t)n);
   L.e = o;
   o = align256(o + 8 * (size_t)n);
   L.added = o;
@@ -202,10 +198,8 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.rev = d_rev;
   D.cap = d_cap;
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
-  D.lab[0] = reinterpret_cast<int *>(base + L.lab0);
-  D.lab[1] = reinterpret_cast<int *>(base + L.lab1);
-  D.act[0] = reinterpret_cast<int *>(base + L.act0);
-  D.act[1] = reinterpret_cast<int *>(base + L.act1);
+  D.vst[0] = reinterpret_cast<int2 *>(base + L.vst0);
+  D.vst[1] = reinterpret_cast<int2 *>(base + L.vst1);
   D.e = reinterpret_cast<long long *>(base + L.e);
   D.added = reinterpret_cast<long long *>(base + L.added);
   D.list[0] = reinterpret_cast<int *>(base + L.list0);

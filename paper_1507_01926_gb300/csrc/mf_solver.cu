@@ -15,7 +15,7 @@
 // Data model (mf_device.cuh): CSR of paired slots with an inline copy of the
 // reverse residual (int2 rr[a] = {res[a], res[rev[a]]}, the "each edge also
 // stores the residual capacity of its reverse edge" layout of Section 4.2),
-// per-vertex int32 label and active-stamp slots, int64 excess.
+// per-vertex {label, active stamp} slots by round parity, int64 excess.
 // Vertex lists are plain arrays filled by warp-aggregated atomics; a list is
 // consumed in tiles of blockDim entries that are binned in shared memory by
 // degree (thread / warp / CTA per vertex).
@@ -77,8 +77,8 @@ __device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigne
 __device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
 
 // label slot p / active stamp slot p of v
-__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return D.lab[p] + v; }
-__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return D.act[p] + v; }
+__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return &D.vst[p][v].x; }
+__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return &D.vst[p][v].y; }
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
@@ -343,12 +343,13 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
       rv[i] = __ldg(&D.rev[beg + i]);
     }
   }
-  const int *labp = D.lab[R.p], *actp = D.act[R.p];
+  const int2 *vsp = D.vst[R.p];
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (rs[i] > 0) {
-      dw[i] = __ldcg(labp + wv[i]);
-      if (__ldcg(actp + wv[i]) == R.r) act |= 1u << i;
+      const int2 x = __ldcg(vsp + wv[i]);
+      dw[i] = x.x;
+      if (x.y == R.r) act |= 1u << i;
     }
   int dp = dv;
   long long to_sink = 0;
@@ -431,8 +432,9 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          dw = __ldcg(lab_ptr(D, w, R.p));
-          wact = __ldcg(act_ptr(D, w, R.p)) == R.r;
+          const int2 x = __ldcg(&D.vst[R.p][w]);
+          dw = x.x;
+          wact = x.y == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -507,8 +509,9 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          dw = __ldcg(lab_ptr(D, w, R.p));
-          wact = __ldcg(act_ptr(D, w, R.p)) == R.r;
+          const int2 x = __ldcg(&D.vst[R.p][w]);
+          dw = x.x;
+          wact = x.y == R.r;
         }
       }
       const bool resid = rs > 0;
@@ -622,8 +625,9 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       }
     } else if (idx < total) {
       const int u = __ldcg(&P[idx - count]);
-      if (__ldcg(act_ptr(D, u, R.p)) != r) {  // not in this working set
-        *lab_ptr(D, u, R.p ^ 1) = __ldcg(lab_ptr(D, u, R.p));
+      const int2 x = __ldcg(&D.vst[R.p][u]);
+      if (x.y != r) {  // not in this working set
+        *lab_ptr(D, u, R.p ^ 1) = x.x;
         const long long ad = take_added(D, u);
         if (ad) atomic_add64(&D.e[u], ad);  // the excess of a non-member may receive pushes now
       }
@@ -679,7 +683,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
   const int *W = list_of(D, gen);
   const int count = list_count(D, gen);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int *labp = D.lab[R.p];
+  const int2 *vsp = D.vst[R.p];
   long long work = 0;
   for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
     const int idx = base + threadIdx.x;
@@ -720,7 +724,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int b = __ldg(&D.row[bv]), e = __ldg(&D.row[bv + 1]);
       int m = INT_MAX;
       for (int a = b + threadIdx.x; a < e; a += blockDim.x)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(labp + __ldg(&D.head[a])) + 1);
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
       m = warp_min(m);
       __syncthreads();
       if (lane == 0) sh.imin[wid] = m;
@@ -737,7 +741,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
       int m = INT_MAX;
       for (int a = b + lane; a < e; a += 32)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(labp + __ldg(&D.head[a])) + 1);
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
       m = warp_min(m);
       if (lane == leader) {
         cls = 0;
@@ -746,7 +750,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
     }
     if (cls == 1) {
       for (int a = beg; a < beg + deg; a++)
-        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(labp + __ldg(&D.head[a])) + 1);
+        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
     }
     if (v >= 0) {
       newl = min(newl, cap_v);
@@ -919,8 +923,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     const int x = __ldcg(lab_ptr(D, v, 0));
     const int c = cap_of(D, v);
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
-    if (d != x) D.lab[0][v] = d;
-    D.lab[1][v] = d;
+    if (d != x) D.vst[0][v].x = d;
+    D.vst[1][v].x = d;
     long long ev = __ldcg(&D.e[v]);
     const long long ad = __ldcg(&D.added[v]);
     if (ad) {
@@ -945,7 +949,7 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   for (int v = tid; v < D.n; v += nthr) {
     const int d = __ldcg(lab_ptr(D, v, p));
-    D.lab[p ^ 1][v] = d;
+    D.vst[p ^ 1][v].x = d;
     const long long ad = __ldcg(&D.added[v]);
     if (ad) {
       D.e[v] = __ldcg(&D.e[v]) + ad;
@@ -1053,10 +1057,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   // excess 0, no stamps.
   for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
   for (int v = tid; v < D.n; v += nthr) {
-    D.lab[0][v] = 0;
-    D.lab[1][v] = 0;
-    D.act[0][v] = -1;
-    D.act[1][v] = -1;
+    D.vst[0][v] = make_int2(0, -1);
+    D.vst[1][v] = make_int2(0, -1);
     D.e[v] = 0;
     D.added[v] = 0;
   }
