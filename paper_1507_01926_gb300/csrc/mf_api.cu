@@ -116,7 +116,7 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vst[0], g->vst[1], g->e, g->added,
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vst[0], g->vst[1], g->ea,
                 g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -161,8 +161,7 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
   for (int k = 0; k < 2; k++)
     if ((rc = dalloc((void **)&g->vst[k], n * 8, "cudaMalloc vertex state"))) return rc;
-  if ((rc = dalloc((void **)&g->e, n * 8, "cudaMalloc excess"))) return rc;
-  if ((rc = dalloc((void **)&g->added, n * 8, "cudaMalloc addedExcess"))) return rc;
+  if ((rc = dalloc((void **)&g->ea, n * 16, "cudaMalloc excess"))) return rc;
   for (int k = 0; k < 3; k++)
     if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
   if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
@@ -257,8 +256,7 @@ Dev make_dev(const mf_graph *g) {
   D.cap = g->cap;
   D.rr = g->rr;
   for (int k = 0; k < 2; k++) D.vst[k] = g->vst[k];
-  D.e = g->e;
-  D.added = g->added;
+  D.ea = g->ea;
   for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
   D.src = g->src;
   D.snk = g->snk;
@@ -593,7 +591,7 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
       if (label[v] > g->n) label[v] = g->n;
   }
   if (excess) {
-    e = cudaMemcpyAsync(excess, g->e, n * 8, cudaMemcpyDeviceToHost, g->stream);
+    e = cudaMemcpy2DAsync(excess, 8, g->ea, 16, 8, n, cudaMemcpyDeviceToHost, g->stream);  // excess halves
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }

@@ -56,8 +56,8 @@ struct Dev {
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
   int2 *vst[2];      // n each: {label, active-round stamp} slots (above)
-  long long *e;      // n: excess
-  long long *added;  // n: excess received while the vertex is in the working set
+  long long *ea;     // 2n: {excess, addedExcess} of v at 2v, 2v + 1 (addedExcess: excess received while
+                     // the vertex is in the working set)
   int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance

@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for n vertices and m slots (offsets from the start).
 struct Layout {
-  size_t ctl, flags, term, rr, vst0, vst1, e, added, list0, list1, list2, total;
+  size_t ctl, flags, term, rr, vst0, vst1, ea, list0, list1, list2, total;
 };
 
 Layout layout(long long n, long long m) {
@@ -56,10 +56,8 @@ Layout layout(long long n, long long m) {
   o = align256(o + 8 * (size_t)n);
   L.vst1 = o;
   o = align256(o + 8 * (size_t)n);
-  L.e = o;
-  o = align256(o + 8 * (size_t)n);
-  L.added = o;
-  o = align256(o + 8 * (size_t)n);
+  L.ea = o;
+  o = align256(o + 16 * (size_t)n);
   L.list0 = o;
   o = align256(o + 4 * (size_t)n);
   L.list1 = o;
@@ -200,8 +198,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
   D.vst[0] = reinterpret_cast<int2 *>(base + L.vst0);
   D.vst[1] = reinterpret_cast<int2 *>(base + L.vst1);
-  D.e = reinterpret_cast<long long *>(base + L.e);
-  D.added = reinterpret_cast<long long *>(base + L.added);
+  D.ea = reinterpret_cast<long long *>(base + L.ea);
   D.list[0] = reinterpret_cast<int *>(base + L.list0);
   D.list[1] = reinterpret_cast<int *>(base + L.list1);
   D.list[2] = reinterpret_cast<int *>(base + L.list2);

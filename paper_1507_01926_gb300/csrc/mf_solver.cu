@@ -82,12 +82,19 @@ __device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return &D.
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
+// excess and addedExcess of v share one 16-byte entry
+__device__ __forceinline__ long long *exc_ptr(const Dev &D, int v) { return D.ea + 2 * (size_t)v; }
+__device__ __forceinline__ long long *add_ptr(const Dev &D, int v) { return D.ea + 2 * (size_t)v + 1; }
+__device__ __forceinline__ longlong2 load_ea(const Dev &D, int v) {
+  return __ldcg(reinterpret_cast<const longlong2 *>(D.ea) + v);
+}
+
 __device__ __forceinline__ void set_err(const Dev &D, int code, int where) {
   if (atomicCAS(&D.ctl->err, 0, code) == 0) atomicExch(&D.ctl->err_where, where);
 }
 
 __device__ __forceinline__ long long take_added(const Dev &D, int v) {
-  return (long long)atomicExch(reinterpret_cast<unsigned long long *>(&D.added[v]), 0ULL);
+  return (long long)atomicExch(reinterpret_cast<unsigned long long *>(add_ptr(D, v)), 0ULL);
 }
 
 __device__ __forceinline__ void atomic_add64(long long *p, long long x) {
@@ -298,14 +305,14 @@ struct RoundCtx {
 // Excess delta reaches w (not the sink). Returns true when w must join the
 // next working set through this call (first discovery this round).
 __device__ __forceinline__ bool deliver(const Dev &D, const RoundCtx &R, int w, bool w_active, long long delta) {
-  atomic_add64(w_active ? &D.added[w] : &D.e[w], delta);
+  atomic_add64(w_active ? add_ptr(D, w) : exc_ptr(D, w), delta);
   return atomicExch(act_ptr(D, w, R.p ^ 1), R.r + 1) != R.r + 1;
 }
 
 __device__ __forceinline__ void finish_vertex(const Dev &D, Shared &sh, const RoundCtx &R, int v, int dp,
                                               long long ex, int cap_v) {
   *lab_ptr(D, v, R.p ^ 1) = dp;
-  D.e[v] = ex;
+  *exc_ptr(D, v) = ex;
   if (ex > 0 && dp < cap_v) {
     if (atomicExch(act_ptr(D, v, R.p ^ 1), R.r + 1) != R.r + 1) qpush(D, sh, R.next, v);
   }
@@ -318,7 +325,7 @@ __device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_
   cg::coalesced_group g = cg::coalesced_threads();
   cg::coalesced_group part = cg::labeled_partition(g, sink);
   const long long sum = cg::reduce(part, to_sink, cg::plus<long long>());
-  if (part.thread_rank() == 0) atomic_add64(&D.e[sink], sum);
+  if (part.thread_rank() == 0) atomic_add64(exc_ptr(D, sink), sum);
 }
 
 // One thread, deg <= KT: arcs cached in registers for all passes.
@@ -329,8 +336,9 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
   // excess: own value plus what neighbours delivered so far; exactly that
   // delivered amount is taken out of addedExcess at the end (later deliveries stay)
   // (simple rounds: only the round-start excess; deliveries are folded in after the pushes)
-  const long long got = D.simple ? 0 : __ldcg(&D.added[v]);
-  long long ex = __ldcg(&D.e[v]) + got;
+  const longlong2 ea = load_ea(D, v);
+  const long long got = D.simple ? 0 : ea.y;
+  long long ex = ea.x + got;
 #pragma unroll
   for (int i = 0; i < KT; i++) {
     wv[i] = 0;
@@ -381,7 +389,7 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
               to_sink += delta;
               sink = wv[i];
             } else {
-              atomic_add64((act >> i) & 1u ? &D.added[wv[i]] : &D.e[wv[i]], delta);
+              atomic_add64((act >> i) & 1u ? add_ptr(D, wv[i]) : exc_ptr(D, wv[i]), delta);
               if (!((tested >> i) & 1u)) {
                 tested |= 1u << i;
                 prev_stamp[i] = atomicExch(act_ptr(D, wv[i], R.p ^ 1), R.r + 1);
@@ -398,9 +406,9 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
     work += deg + D.beta;
     if (dp >= cap_v) break;
   }
-  if (got) atomic_add64(&D.added[v], -got);
+  if (got) atomic_add64(add_ptr(D, v), -got);
   if (D.simple)
-    D.e[v] = ex;  // label and re-activation: relabel_phase
+    *exc_ptr(D, v) = ex;  // label and re-activation: relabel_phase
   else
     finish_vertex(D, sh, R, v, dp, ex, cap_v);
 #pragma unroll
@@ -416,7 +424,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
   long long ex = 0;
-  if (lane == 0) ex = __ldcg(&D.e[v]) + (D.simple ? 0 : take_added(D, v));
+  if (lane == 0) ex = __ldcg(exc_ptr(D, v)) + (D.simple ? 0 : take_added(D, v));
   ex = __shfl_sync(FULL, ex, 0);
   int dp = dv;
   long long to_sink = 0;
@@ -476,7 +484,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
   }
   if (lane == 0) {
     if (D.simple)
-      D.e[v] = ex;
+      *exc_ptr(D, v) = ex;
     else
       finish_vertex(D, sh, R, v, dp, ex, cap_v);
   }
@@ -492,7 +500,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
   const int beg = __ldg(&D.row[v]);
   const int deg = __ldg(&D.row[v + 1]) - beg;
   __syncthreads();
-  if (threadIdx.x == 0) sh.lsum[0] = __ldcg(&D.e[v]) + (D.simple ? 0 : take_added(D, v));
+  if (threadIdx.x == 0) sh.lsum[0] = __ldcg(exc_ptr(D, v)) + (D.simple ? 0 : take_added(D, v));
   __syncthreads();
   long long ex = sh.lsum[0];
   int dp = dv;
@@ -570,7 +578,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
   }
   if (threadIdx.x == 0) {
     if (D.simple)
-      D.e[v] = ex;
+      *exc_ptr(D, v) = ex;
     else
       finish_vertex(D, sh, R, v, dp, ex, cap_v);
   }
@@ -584,7 +592,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
 __device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int v, int dv) {
   *lab_ptr(D, v, R.p ^ 1) = dv;
   const long long ad = take_added(D, v);
-  if (ad) D.e[v] = __ldcg(&D.e[v]) + ad;
+  if (ad) *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
 }
 
 // One round over a combined index space: entries [0, count) are the working
@@ -629,7 +637,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       if (x.y != r) {  // not in this working set
         *lab_ptr(D, u, R.p ^ 1) = x.x;
         const long long ad = take_added(D, u);
-        if (ad) atomic_add64(&D.e[u], ad);  // the excess of a non-member may receive pushes now
+        if (ad) atomic_add64(exc_ptr(D, u), ad);  // the excess of a non-member may receive pushes now
       }
     }
     for (bool any = __syncthreads_or(cls == 3); any;) {  // CTA per vertex
@@ -693,9 +701,9 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int dv = __ldcg(lab_ptr(D, v, R.p));
       cap_v = cap_of(D, v);
       // Section 3 step 4 for this vertex: the excess it received this round joins its excess now
-      const long long ex_own = __ldcg(&D.e[v]);
+      const long long ex_own = __ldcg(exc_ptr(D, v));
       const long long ad = dv >= cap_v ? 0 : take_added(D, v);
-      if (ad) D.e[v] = ex_own + ad;
+      if (ad) *exc_ptr(D, v) = ex_own + ad;
       if (dv >= cap_v) {
         v = -1;  // retired in the push step
       } else if (ex_own == 0) {
@@ -864,7 +872,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     int x = UNV;
     if (excess_seeds) {
       const int d = __ldcg(lab_ptr(D, v, 0));
-      if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) > 0) {
+      if (d >= 1 && d <= cap_of(D, v) && __ldcg(exc_ptr(D, v)) > 0) {
         x = 0;
         qpush(D, sh, next, v);
       }
@@ -925,12 +933,13 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
     if (d != x) D.vst[0][v].x = d;
     D.vst[1][v].x = d;
-    long long ev = __ldcg(&D.e[v]);
-    const long long ad = __ldcg(&D.added[v]);
+    const longlong2 ea = load_ea(D, v);
+    long long ev = ea.x;
+    const long long ad = ea.y;
     if (ad) {
       ev += ad;
-      D.e[v] = ev;
-      D.added[v] = 0;
+      *exc_ptr(D, v) = ev;
+      *add_ptr(D, v) = 0;
     }
     if (d > 0 && d < c && ev > 0) {
       *act_ptr(D, v, p) = r;
@@ -950,10 +959,10 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
   for (int v = tid; v < D.n; v += nthr) {
     const int d = __ldcg(lab_ptr(D, v, p));
     D.vst[p ^ 1][v].x = d;
-    const long long ad = __ldcg(&D.added[v]);
+    const long long ad = __ldcg(add_ptr(D, v));
     if (ad) {
-      D.e[v] = __ldcg(&D.e[v]) + ad;
-      D.added[v] = 0;
+      *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
+      *add_ptr(D, v) = 0;
     }
   }
   return grid_sync(D, sh, 12);
@@ -1059,8 +1068,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   for (int v = tid; v < D.n; v += nthr) {
     D.vst[0][v] = make_int2(0, -1);
     D.vst[1][v] = make_int2(0, -1);
-    D.e[v] = 0;
-    D.added[v] = 0;
+    *exc_ptr(D, v) = 0;
+    *add_ptr(D, v) = 0;
   }
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
@@ -1076,7 +1085,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
         const int cr = __ldg(&D.cap[ra]);
         D.rr[a] = make_int2(0, cr + c);
         D.rr[ra] = make_int2(cr + c, 0);
-        atomic_add64(&D.e[w], c);
+        atomic_add64(exc_ptr(D, w), c);
       }
     }
     ok = grid_sync(D, sh, 1);
@@ -1087,7 +1096,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   if (ok && D.mode == MODE_SOLVE) {
     if (tid == 0) D.ctl->t_preflow = gtimer();
     for (int k = tid; k < D.ninst; k += nthr) {
-      const long long val = __ldcg(&D.e[D.snk[k]]);
+      const long long val = __ldcg(&D.ea[2 * (size_t)D.snk[k]]);
       if (D.out_value) D.out_value[k] = val;
       if (k == 0) D.ctl->value = val;
     }
@@ -1101,7 +1110,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
         long long left = 0;
         for (int v = tid; v < D.n; v += nthr) {
           const int d = __ldcg(lab_ptr(D, v, 0));
-          if (d >= 1 && d <= cap_of(D, v) && __ldcg(&D.e[v]) != 0) left++;
+          if (d >= 1 && d <= cap_of(D, v) && __ldcg(exc_ptr(D, v)) != 0) left++;
         }
         left = block_sum(left, sh);
         if (threadIdx.x == 0 && left) atomic_add64(&D.ctl->leftover, left);
