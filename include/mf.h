@@ -280,7 +280,7 @@ void mf_service_destroy(mf_service *svc);
  * enqueued on `stream` (a cudaStream_t); the call returns when the solve is
  * done. All working state lives in one static device scratch area of 32 MiB
  * that every GPU loading the library holds until the process exits; a graph
- * needing more (about 48 bytes per vertex + 8 per slot) is rejected with
+ * needing more (about 52 bytes per vertex + 8 per slot) is rejected with
  * MF_ERR_TOO_LARGE before any work. The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine. The first call on each device looks
  * up the scratch area's device address (cudaGetSymbolAddress); make that first

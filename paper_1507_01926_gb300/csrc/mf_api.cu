@@ -116,7 +116,7 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vst[0], g->vst[1], g->ea,
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vst[0], g->vst[1], g->blab, g->ea,
                 g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -161,6 +161,7 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
   for (int k = 0; k < 2; k++)
     if ((rc = dalloc((void **)&g->vst[k], n * 8, "cudaMalloc vertex state"))) return rc;
+  if ((rc = dalloc((void **)&g->blab, n * 4, "cudaMalloc BFS labels"))) return rc;
   if ((rc = dalloc((void **)&g->ea, n * 16, "cudaMalloc excess"))) return rc;
   for (int k = 0; k < 3; k++)
     if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
@@ -256,6 +257,7 @@ Dev make_dev(const mf_graph *g) {
   D.cap = g->cap;
   D.rr = g->rr;
   for (int k = 0; k < 2; k++) D.vst[k] = g->vst[k];
+  D.blab = g->blab;
   D.ea = g->ea;
   for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
   D.src = g->src;

@@ -43,8 +43,8 @@ struct Ctl {
 // stamp} (one 8-byte gather gives both, four vertices per 32-byte sector).
 // Round r reads the label of every vertex from slot r & 1 and a discharged
 // vertex writes d' into slot (r + 1) & 1; a vertex is in the working set of
-// round r iff vst[r & 1][v].y == r. Slot 0 holds the labels during a BFS and
-// at phase ends.
+// round r iff vst[r & 1][v].y == r. A BFS works on its own label array blab;
+// both slots hold the same labels at phase ends.
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
@@ -56,6 +56,7 @@ struct Dev {
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
   int2 *vst[2];      // n each: {label, active-round stamp} slots (above)
+  int *blab;         // n: BFS labels (dense, so that BFS gathers stay in L2); copied into vst by the rebuild
   long long *ea;     // 2n: {excess, addedExcess} of v at 2v, 2v + 1 (addedExcess: excess received while
                      // the vertex is in the working set)
   int *list[3];      // vertex lists, generation g uses list[g % 3]

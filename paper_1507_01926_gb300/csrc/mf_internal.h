@@ -21,6 +21,7 @@ struct mf_graph {
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
   int2 *rr = nullptr;
   int2 *vst[2] = {nullptr, nullptr};
+  int *blab = nullptr;
   long long *ea = nullptr;     // {excess, addedExcess} per vertex
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;

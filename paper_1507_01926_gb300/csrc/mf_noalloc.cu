@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for n vertices and m slots (offsets from the start).
 struct Layout {
-  size_t ctl, flags, term, rr, vst0, vst1, ea, list0, list1, list2, total;
+  size_t ctl, flags, term, rr, vst0, vst1, blab, ea, list0, list1, list2, total;
 };
 
 Layout layout(long long n, long long m) {
@@ -56,6 +56,8 @@ Layout layout(long long n, long long m) {
   o = align256(o + 8 * (size_t)n);
   L.vst1 = o;
   o = align256(o + 8 * (size_t)n);
+  L.blab = o;
+  o = align256(o + 4 * (size_t)n);
   L.ea = o;
   o = align256(o + 16 * (size_t)n);
   L.list0 = o;
@@ -148,7 +150,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   const Layout L = layout(n, m);
   if (L.total > NOALLOC_SCRATCH_BYTES)
     return fail(MF_ERR_TOO_LARGE,
-                "graph needs %zu bytes of scratch (about 48 per vertex + 8 per slot); the fixed area holds %zu",
+                "graph needs %zu bytes of scratch (about 52 per vertex + 8 per slot); the fixed area holds %zu",
                 L.total, NOALLOC_SCRATCH_BYTES);
   unsigned char *base = nullptr;
   int rc = scratch_base(&base);
@@ -198,6 +200,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
   D.vst[0] = reinterpret_cast<int2 *>(base + L.vst0);
   D.vst[1] = reinterpret_cast<int2 *>(base + L.vst1);
+  D.blab = reinterpret_cast<int *>(base + L.blab);
   D.ea = reinterpret_cast<long long *>(base + L.ea);
   D.list[0] = reinterpret_cast<int *>(base + L.list0);
   D.list[1] = reinterpret_cast<int *>(base + L.list1);

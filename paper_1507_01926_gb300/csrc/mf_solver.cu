@@ -784,8 +784,8 @@ __device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int lvl
   const int w = __ldg(&D.head[a]);
   const int2 x = __ldcg(&D.rr[a]);
   const int cf = reverse ? x.y : x.x;
-  if (cf > 0 && __ldcg(lab_ptr(D, w, 0)) == UNV) {
-    if (atomicCAS(lab_ptr(D, w, 0), UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
+  if (cf > 0 && __ldcg(D.blab + w) == UNV) {
+    if (atomicCAS(D.blab + w, UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
   }
 }
 
@@ -804,10 +804,10 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
     }
   }
 #pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(lab_ptr(D, w[i], 0)) : 0;
+  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(D.blab + w[i]) : 0;
   // all CAS first (in flight together), then the appends
 #pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = (cf[i] > 0 && lab[i] == UNV) ? atomicCAS(lab_ptr(D, w[i], 0), UNV, lvl + 1) : 0;
+  for (int i = 0; i < KT; i++) lab[i] = (cf[i] > 0 && lab[i] == UNV) ? atomicCAS(D.blab + w[i], UNV, lvl + 1) : 0;
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (cf[i] > 0 && lab[i] == UNV) qpush(D, sh, next, w[i]);
@@ -877,14 +877,14 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
         qpush(D, sh, next, v);
       }
     }
-    *lab_ptr(D, v, 0) = x;
+    D.blab[v] = x;
   }
   qflush(D, sh, next);
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
-    *lab_ptr(D, seeds[i], 0) = 0;
-    if (blockers) *lab_ptr(D, blockers[i], 0) = UNV + 1;
+    D.blab[seeds[i]] = 0;
+    if (blockers) D.blab[blockers[i]] = UNV + 1;
   }
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nterm; i += blockDim.x) append(D, next, seeds[i]);
@@ -928,10 +928,10 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     D.ctl->grs++;
   }
   for (int v = tid; v < D.n; v += nthr) {
-    const int x = __ldcg(lab_ptr(D, v, 0));
+    const int x = __ldcg(D.blab + v);
     const int c = cap_of(D, v);
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
-    if (d != x) D.vst[0][v].x = d;
+    D.vst[0][v].x = d;
     D.vst[1][v].x = d;
     const longlong2 ea = load_ea(D, v);
     long long ev = ea.x;
@@ -1130,7 +1130,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
           unsigned bits = 0;
           for (int j = 0; j < 32; j++) {
             const int v = wd * 32 + j;
-            if (v < D.n && __ldcg(lab_ptr(D, v, 0)) != UNV) bits |= 1u << j;
+            if (v < D.n && __ldcg(D.blab + v) != UNV) bits |= 1u << j;
           }
           D.out_cut[wd] = bits;
         }
