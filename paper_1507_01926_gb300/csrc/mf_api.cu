@@ -100,6 +100,14 @@ __global__ void k_check_pairs(int n, long long m, const int *row, const int *hea
   if (cnt) atomicAdd(m_arcs, cnt);
 }
 
+// Largest out-degree (slots) of a vertex other than s and t.
+__global__ void k_max_degree(int n, const int *row, int s, int t, unsigned *out) {
+  unsigned mx = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (v != s && v != t) mx = max(mx, (unsigned)(row[v + 1] - row[v]));
+  if (mx) atomicMax(out, mx);
+}
+
 static int flags_to_status(unsigned f) {
   if (f & (V_ROW | V_HEAD | V_REV | V_CAP)) {
     return fail(MF_ERR_INVALID_ARG, "invalid graph:%s%s%s%s", (f & V_ROW) ? " row_offsets not a valid CSR;" : "",
@@ -200,6 +208,7 @@ int validate_on_device(mf_graph *g, const long long *row64, const long long *rev
   }
   if (h[0] == 0 && g->m > 0) {
     k_check_pairs<<<Gm, T, 0, st>>>(g->n, g->m, g->row, g->head, g->cap, g->rev, flags, marcs);
+    k_max_degree<<<Gn, T, 0, st>>>(g->n, g->row, g->s, g->t, flags + 1);
     e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -209,6 +218,7 @@ int validate_on_device(mf_graph *g, const long long *row64, const long long *rev
   }
   cudaFree(flags);
   g->m_arcs = (long long)((unsigned long long)h[2] | ((unsigned long long)h[3] << 32));
+  g->max_degree = h[1];
   return flags_to_status(h[0]);
 }
 
@@ -271,6 +281,7 @@ Dev make_dev(const mf_graph *g) {
   D.gr_threshold = thr > 9.0e18 ? (long long)9e18 : (long long)thr;
   D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
   D.simple = g->opt.simple_rounds ? 1 : 0;
+  D.cta_vertices = g->max_degree > (long long)g->opt.bin_warp ? 1 : 0;
   D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "mf.h"
@@ -125,6 +126,13 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
   cudaFree(row64);
   cudaFree(rev64);
   if (rc) return rc;
+  long long maxdeg = 0;  // over all instances, sources and sinks excluded
+  for (int k = 0; k < count; k++) {
+    const mf_graph_desc &d = descs[k];
+    for (int v = 0; v < d.n; v++)
+      if (v != d.s && v != d.t) maxdeg = std::max(maxdeg, (long long)(d.row_offsets[v + 1] - d.row_offsets[v]));
+  }
+  g->max_degree = maxdeg;
   return launch_config(g);
 }
 

@@ -77,6 +77,8 @@ struct Dev {
   int final_gr;
   int cut_only;
   int simple;              // 1: the simple synchronous rounds of Section 3 (push pass, then one relabel)
+  int cta_vertices;        // 0: no vertex other than a source or sink has more than bin_warp slots, so no
+                           //    discharge needs a whole CTA (the CTA-wide check is skipped)
   // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
   int2 *trace;
   long long trace_cap;

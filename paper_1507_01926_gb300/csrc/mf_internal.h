@@ -14,6 +14,7 @@ struct mf_graph {
   int n_cap = 0;               // label cap of a single instance (n)
   long long n_total_for_gr = 0;  // n in the relabel threshold alpha * n + m
   long long m_arcs = 0;        // slots with positive capacity
+  long long max_degree = 0;    // largest slot count of a vertex that is not a source or a sink
   mf_options opt{};
   mf_stats stats{};
   int grid = 0, block = 0;

@@ -98,6 +98,13 @@ __global__ void k_noalloc_rows(int n, int m, const int *row, unsigned *flags) {
   }
 }
 
+__global__ void k_noalloc_maxdeg(int n, const int *row, int s, int t, unsigned *out) {
+  unsigned mx = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (v != s && v != t) mx = max(mx, (unsigned)(row[v + 1] - row[v]));
+  if (mx) atomicMax(out, mx);
+}
+
 __global__ void k_noalloc_slots(int n, int m, const int *row, const int *head, const int *cap, const int *rev,
                                 unsigned *flags, unsigned long long *m_arcs) {
   unsigned f = 0;
@@ -124,12 +131,14 @@ __global__ void k_noalloc_slots(int n, int m, const int *row, const int *head, c
   if (cnt) atomicAdd(m_arcs, cnt);
 }
 
-int read_flags(unsigned char *dev_flags, cudaStream_t st, unsigned *f, unsigned long long *marcs) {
+int read_flags(unsigned char *dev_flags, cudaStream_t st, unsigned *f, unsigned long long *marcs,
+               unsigned *maxdeg) {
   unsigned h[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h, dev_flags, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "graph validation");
   *f = h[0];
+  *maxdeg = h[1];
   *marcs = (unsigned long long)h[2] | ((unsigned long long)h[3] << 32);
   return MF_OK;
 }
@@ -167,13 +176,15 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   const int T = 256;
   k_noalloc_rows<<<(n + 1 + T - 1) / T < 4096 ? (n + 1 + T - 1) / T : 4096, T, 0, st>>>(n, m, d_row,
                                                                                       (unsigned *)flags);
-  unsigned f = 0;
+  unsigned f = 0, maxdeg = 0;
   unsigned long long marcs = 0;
-  if ((rc = read_flags(flags, st, &f, &marcs))) return rc;
+  if ((rc = read_flags(flags, st, &f, &marcs, &maxdeg))) return rc;
   if (!f && m > 0) {
     k_noalloc_slots<<<(m + T - 1) / T < 4096 ? (m + T - 1) / T : 4096, T, 0, st>>>(
         n, m, d_row, d_head, d_cap, d_rev, (unsigned *)flags, (unsigned long long *)(flags + 8));
-    if ((rc = read_flags(flags, st, &f, &marcs))) return rc;
+    k_noalloc_maxdeg<<<(n + T - 1) / T < 4096 ? (n + T - 1) / T : 4096, T, 0, st>>>(n, d_row, s, t,
+                                                                                   (unsigned *)flags + 1);
+    if ((rc = read_flags(flags, st, &f, &marcs, &maxdeg))) return rc;
   }
   if (f & (N_ROW | N_HEAD | N_REV | N_CAP))
     return fail(MF_ERR_INVALID_ARG, "invalid graph (flags 0x%x): row offsets, head, rev or capacity", f);
@@ -218,6 +229,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.max_rounds = 2000000LL;
   D.timeout_ns = (unsigned long long)o.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
+  D.cta_vertices = maxdeg > (unsigned)o.bin_warp ? 1 : 0;
   D.out_value = reinterpret_cast<long long *>(d_value);
   D.out_flow = d_flow;
   D.out_cut = d_cut;

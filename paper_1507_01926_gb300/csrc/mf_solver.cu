@@ -640,7 +640,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
         if (ad) atomic_add64(exc_ptr(D, u), ad);  // the excess of a non-member may receive pushes now
       }
     }
-    for (bool any = __syncthreads_or(cls == 3); any;) {  // CTA per vertex
+    for (bool any = D.cta_vertices && __syncthreads_or(cls == 3); any;) {  // CTA per vertex
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
       if (cls == 3) sh.pick = threadIdx.x;
@@ -716,7 +716,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       }
     }
     int newl = INT_MAX;
-    for (bool any = __syncthreads_or(cls == 3); any;) {  // CTA per vertex
+    for (bool any = D.cta_vertices && __syncthreads_or(cls == 3); any;) {  // CTA per vertex
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
       if (cls == 3) sh.pick = threadIdx.x;
