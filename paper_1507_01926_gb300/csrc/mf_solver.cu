@@ -184,6 +184,16 @@ __device__ __forceinline__ void qpush(const Dev &D, Shared &sh, int gen, int val
     append(D, gen, val);
 }
 
+// Entries of a list that one CTA takes per sweep: a whole block when the list
+// fills the grid; otherwise the list is spread evenly over all CTAs in warp
+// multiples, so that a short list loads every SM's memory pipeline a little
+// instead of a few SMs heavily.
+__device__ __forceinline__ int sweep_chunk(int total) {
+  const int per = (int)(((long long)total + gridDim.x - 1) / gridDim.x);
+  const int w = (per + 31) & ~31;
+  return w < (int)blockDim.x ? w : (int)blockDim.x;
+}
+
 // All threads of the CTA call this at the end of a phase that appended to gen:
 // publishes the staged appends and adds the CTA's sum of `work` to *work_dst
 // (nullable) with two CTA barriers.
@@ -615,8 +625,9 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
   const int total = count + cp;
   const int lane = threadIdx.x & 31;
   long long work = 0;
-  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-    const int idx = base + threadIdx.x;
+  const int per = sweep_chunk(total);
+  for (int base = blockIdx.x * per; base < total; base += gridDim.x * per) {
+    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
     int v = -1, beg = 0, deg = 0, cls = 0, dv = 0, cap_v = 0;
     if (idx < count) {
       v = __ldcg(&W[idx]);
@@ -693,8 +704,9 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int2 *vsp = D.vst[R.p];
   long long work = 0;
-  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-    const int idx = base + threadIdx.x;
+  const int per = sweep_chunk(count);
+  for (int base = blockIdx.x * per; base < count; base += gridDim.x * per) {
+    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
     int v = -1, beg = 0, deg = 0, cls = 0, cap_v = 0;
     if (idx < count) {
       v = __ldcg(&W[idx]);
@@ -784,9 +796,7 @@ __device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int lvl
   const int w = __ldg(&D.head[a]);
   const int2 x = __ldcg(&D.rr[a]);
   const int cf = reverse ? x.y : x.x;
-  if (cf > 0 && __ldcg(D.blab + w) == UNV) {
-    if (atomicCAS(D.blab + w, UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
-  }
+  if (cf > 0 && atomicCAS(D.blab + w, UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
 }
 
 // One thread, deg <= KT, loads issued together.
@@ -803,11 +813,9 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
       cf[i] = reverse ? x.y : x.x;
     }
   }
-#pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? __ldcg(D.blab + w[i]) : 0;
   // all CAS first (in flight together), then the appends
 #pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = (cf[i] > 0 && lab[i] == UNV) ? atomicCAS(D.blab + w[i], UNV, lvl + 1) : 0;
+  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? atomicCAS(D.blab + w[i], UNV, lvl + 1) : 0;
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (cf[i] > 0 && lab[i] == UNV) qpush(D, sh, next, w[i]);
@@ -819,8 +827,9 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
   const int count = list_count(D, gen);
   if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
   const int lane = threadIdx.x & 31;
-  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-    const int idx = base + threadIdx.x;
+  const int per = sweep_chunk(count);
+  for (int base = blockIdx.x * per; base < count; base += gridDim.x * per) {
+    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
     const int v = idx < count ? __ldcg(&F[idx]) : -1;
     int beg = 0, deg = 0, cls = 0;
     if (v >= 0) {
