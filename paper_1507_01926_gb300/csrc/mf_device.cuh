@@ -1,6 +1,7 @@
 // Device-side data model of the solver (shared by the kernels and the host
 // launch code). Everything is plain integer state resident in HBM.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 namespace mf {
@@ -36,6 +37,8 @@ struct Ctl {
   unsigned long long t_start, t_preflow, t_end;  // %globaltimer, ns
   int stopped_round;   // MODE_ROUNDS: rounds run
 };
+// the kernel reads cnt as one int4 and gr_req as one int2
+static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0, "Ctl layout");
 
 // Device view of one (possibly multi-instance) graph.
 //

@@ -118,7 +118,6 @@ __device__ __forceinline__ void push_res(const Dev &D, int a, int ra, int delta)
   atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[ra]), d64 - (d64 << 32));
 }
 
-__device__ __forceinline__ int list_count(const Dev &D, int gen) { return min(__ldcg(&D.ctl->cnt[gen & 3]), D.n); }
 __device__ __forceinline__ int *list_of(const Dev &D, int gen) { return D.list[gen % 3]; }
 
 // Appends one value per calling thread to the list of generation gen with one
@@ -161,8 +160,19 @@ __device__ __forceinline__ long long warp_incl_scan(long long x, int lane) {
 
 constexpr int QCAP = 2048;  // per-CTA staging of list appends
 
+// Control words as they stood at the last grid barrier, read once by thread 0
+// and shared with the CTA: the error word, the list sizes, the per-round
+// relabel work and the time-based relabel requests.
+struct Snap {
+  int err;
+  int cnt[4];
+  long long work[3];
+  int gr_req[2];
+};
+
 struct Shared {
   unsigned long long bars;  // grid barriers passed by this CTA
+  Snap snap;
   int pick;
   int flag;
   int qn;                   // staged appends (may exceed QCAP; the excess went straight to the list)
@@ -284,9 +294,30 @@ __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
       }
     }
     sh.bars++;
+    // one round trip for every control word the next phase reads
+    const Ctl *cw = D.ctl;
+    const int err = vol_read(&cw->err);
+    const int4 k = __ldcg(reinterpret_cast<const int4 *>(cw->cnt));
+    const long long w0 = __ldcg(&cw->work[0]), w1 = __ldcg(&cw->work[1]), w2 = __ldcg(&cw->work[2]);
+    const int2 q = __ldcg(reinterpret_cast<const int2 *>(cw->gr_req));
+    sh.snap.err = err;
+    sh.snap.cnt[0] = k.x;
+    sh.snap.cnt[1] = k.y;
+    sh.snap.cnt[2] = k.z;
+    sh.snap.cnt[3] = k.w;
+    sh.snap.work[0] = w0;
+    sh.snap.work[1] = w1;
+    sh.snap.work[2] = w2;
+    sh.snap.gr_req[0] = q.x;
+    sh.snap.gr_req[1] = q.y;
   }
   __syncthreads();
-  return vol_read(&D.ctl->err) == 0;
+  return sh.snap.err == 0;
+}
+
+// Size of the list of generation gen as of the last grid barrier.
+__device__ __forceinline__ int list_count(const Dev &D, const Shared &sh, int gen) {
+  return min(sh.snap.cnt[gen & 3], D.n);
 }
 
 struct TStat {
@@ -619,9 +650,9 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
     D.ctl->work[(rnd + 1) % 3] = 0;
   }
   const int *W = list_of(D, gen);
-  const int count = list_count(D, gen);
+  const int count = list_count(D, sh, gen);
   const int *P = list_of(D, gen - 1);
-  const int cp = prev_valid ? list_count(D, gen - 1) : 0;
+  const int cp = prev_valid ? list_count(D, sh, gen - 1) : 0;
   const int total = count + cp;
   const int lane = threadIdx.x & 31;
   long long work = 0;
@@ -700,7 +731,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
 __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd, TStat &st) {
   const RoundCtx R{r, r & 1, gen + 1};
   const int *W = list_of(D, gen);
-  const int count = list_count(D, gen);
+  const int count = list_count(D, sh, gen);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int2 *vsp = D.vst[R.p];
   long long work = 0;
@@ -824,7 +855,7 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
   const int *F = list_of(D, gen);
   const int next = gen + 1;
-  const int count = list_count(D, gen);
+  const int count = list_count(D, sh, gen);
   if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
   const int lane = threadIdx.x & 31;
   const int per = sweep_chunk(count);
@@ -901,7 +932,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   for (int lvl = 0;; lvl++) {
-    const int fcount = list_count(D, gen);
+    const int fcount = list_count(D, sh, gen);
     if (fcount == 0) break;
     if (timer && D.trace_lv) {
       const long long k = D.ctl->levels;
@@ -1001,7 +1032,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       time_req = false;
       prev_valid = false;
     }
-    const int count = list_count(D, gen);
+    const int count = list_count(D, sh, gen);
     if (count == 0) {
       if (fresh) break;
       since_gr = LLONG_MAX;
@@ -1033,8 +1064,8 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       D.ctl->t_dis += t3 - t0;
       D.ctl->t_rwait += t3 - tp;
     }
-    since_gr += __ldcg(&D.ctl->work[rnd % 3]);
-    time_req = __ldcg(&D.ctl->gr_req[rnd & 1]) != 0;
+    since_gr += sh.snap.work[rnd % 3];
+    time_req = sh.snap.gr_req[rnd & 1] != 0;
     r++;
     gen++;
     rnd++;
