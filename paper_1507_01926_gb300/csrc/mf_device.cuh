@@ -42,12 +42,14 @@ static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0, "C
 
 // Device view of one (possibly multi-instance) graph.
 //
-// Vertex state: two slots by round parity, vst[p][v] = {label, active-round
-// stamp} (one 8-byte gather gives both, four vertices per 32-byte sector).
-// Round r reads the label of every vertex from slot r & 1 and a discharged
-// vertex writes d' into slot (r + 1) & 1; a vertex is in the working set of
-// round r iff vst[r & 1][v].y == r. A BFS works on its own label array blab;
-// both slots hold the same labels at phase ends.
+// Vertex state: two slots by round parity, each {label, active-round stamp},
+// interleaved per vertex: vs[v] = {label 0, stamp 0, label 1, stamp 1}, so that
+// the slot a round reads and the slot it writes share one 32-byte sector (the
+// gather of a neighbour's label brings in the stamp a push then sets). Round r
+// reads the label of every vertex from slot r & 1 and a discharged vertex
+// writes d' into slot (r + 1) & 1; a vertex is in the working set of round r
+// iff its stamp in slot r & 1 equals r. A BFS works on its own label array
+// blab; both slots hold the same labels at phase ends.
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
@@ -58,8 +60,8 @@ struct Dev {
   const int *__restrict__ rev;   // m
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
-  int2 *vst[2];      // n each: {label, active-round stamp} slots (above)
-  int *blab;         // n: BFS labels (dense, so that BFS gathers stay in L2); copied into vst by the rebuild
+  int4 *vs;          // n: {label 0, stamp 0, label 1, stamp 1} (above)
+  int *blab;         // n: BFS labels (dense, so that BFS gathers stay in L2); copied into both label slots by the rebuild
   long long *ea;     // 2n: {excess, addedExcess} of v at 2v, 2v + 1 (addedExcess: excess received while
                      // the vertex is in the working set)
   int *list[3];      // vertex lists, generation g uses list[g % 3]

@@ -21,7 +21,7 @@ struct mf_graph {
   // device state
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
   int2 *rr = nullptr;
-  int2 *vst[2] = {nullptr, nullptr};
+  int4 *vs = nullptr;  // {label 0, stamp 0, label 1, stamp 1} per vertex
   int *blab = nullptr;
   long long *ea = nullptr;     // {excess, addedExcess} per vertex
   int *list[3] = {nullptr, nullptr, nullptr};

@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for n vertices and m slots (offsets from the start).
 struct Layout {
-  size_t ctl, flags, term, rr, vst0, vst1, blab, ea, list0, list1, list2, total;
+  size_t ctl, flags, term, rr, vs, blab, ea, list0, list1, list2, total;
 };
 
 Layout layout(long long n, long long m) {
@@ -52,10 +52,8 @@ Layout layout(long long n, long long m) {
   o = align256(o + 8);
   L.rr = o;
   o = align256(o + 8 * (size_t)m);
-  L.vst0 = o;
-  o = align256(o + 8 * (size_t)n);
-  L.vst1 = o;
-  o = align256(o + 8 * (size_t)n);
+  L.vs = o;
+  o = align256(o + 16 * (size_t)n);
   L.blab = o;
   o = align256(o + 4 * (size_t)n);
   L.ea = o;
@@ -209,8 +207,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.rev = d_rev;
   D.cap = d_cap;
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
-  D.vst[0] = reinterpret_cast<int2 *>(base + L.vst0);
-  D.vst[1] = reinterpret_cast<int2 *>(base + L.vst1);
+  D.vs = reinterpret_cast<int4 *>(base + L.vs);
   D.blab = reinterpret_cast<int *>(base + L.blab);
   D.ea = reinterpret_cast<long long *>(base + L.ea);
   D.list[0] = reinterpret_cast<int *>(base + L.list0);

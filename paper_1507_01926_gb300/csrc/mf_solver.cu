@@ -77,8 +77,12 @@ __device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigne
 __device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
 
 // label slot p / active stamp slot p of v
-__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return &D.vst[p][v].x; }
-__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return &D.vst[p][v].y; }
+__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return reinterpret_cast<int *>(D.vs + v) + 2 * p; }
+__device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return lab_ptr(D, v, p) + 1; }
+// {label, stamp} of v in slot p
+__device__ __forceinline__ int2 load_slot(const Dev &D, int p, int v) {
+  return __ldcg(reinterpret_cast<const int2 *>(D.vs + v) + p);
+}
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
@@ -392,11 +396,10 @@ __device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, in
       rv[i] = __ldg(&D.rev[beg + i]);
     }
   }
-  const int2 *vsp = D.vst[R.p];
 #pragma unroll
   for (int i = 0; i < KT; i++)
     if (rs[i] > 0) {
-      const int2 x = __ldcg(vsp + wv[i]);
+      const int2 x = load_slot(D, R.p, wv[i]);
       dw[i] = x.x;
       if (x.y == R.r) act |= 1u << i;
     }
@@ -481,7 +484,7 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          const int2 x = __ldcg(&D.vst[R.p][w]);
+          const int2 x = load_slot(D, R.p, w);
           dw = x.x;
           wact = x.y == R.r;
         }
@@ -558,7 +561,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
         w = __ldg(&D.head[beg + i]);
         rs = __ldcg(&D.rr[beg + i]).x;
         if (rs > 0) {
-          const int2 x = __ldcg(&D.vst[R.p][w]);
+          const int2 x = load_slot(D, R.p, w);
           dw = x.x;
           wact = x.y == R.r;
         }
@@ -675,7 +678,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       }
     } else if (idx < total) {
       const int u = __ldcg(&P[idx - count]);
-      const int2 x = __ldcg(&D.vst[R.p][u]);
+      const int2 x = load_slot(D, R.p, u);
       if (x.y != r) {  // not in this working set
         *lab_ptr(D, u, R.p ^ 1) = x.x;
         const long long ad = take_added(D, u);
@@ -733,7 +736,6 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
   const int *W = list_of(D, gen);
   const int count = list_count(D, sh, gen);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int2 *vsp = D.vst[R.p];
   long long work = 0;
   const int per = sweep_chunk(count);
   for (int base = blockIdx.x * per; base < count; base += gridDim.x * per) {
@@ -775,7 +777,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int b = __ldg(&D.row[bv]), e = __ldg(&D.row[bv + 1]);
       int m = INT_MAX;
       for (int a = b + threadIdx.x; a < e; a += blockDim.x)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
       m = warp_min(m);
       __syncthreads();
       if (lane == 0) sh.imin[wid] = m;
@@ -792,7 +794,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
       int m = INT_MAX;
       for (int a = b + lane; a < e; a += 32)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
+        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
       m = warp_min(m);
       if (lane == leader) {
         cls = 0;
@@ -801,7 +803,7 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
     }
     if (cls == 1) {
       for (int a = beg; a < beg + deg; a++)
-        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(vsp + __ldg(&D.head[a])).x + 1);
+        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
     }
     if (v >= 0) {
       newl = min(newl, cap_v);
@@ -971,8 +973,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     const int x = __ldcg(D.blab + v);
     const int c = cap_of(D, v);
     const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
-    D.vst[0][v].x = d;
-    D.vst[1][v].x = d;
+    *lab_ptr(D, v, 0) = d;
+    *lab_ptr(D, v, 1) = d;
     const longlong2 ea = load_ea(D, v);
     long long ev = ea.x;
     const long long ad = ea.y;
@@ -998,7 +1000,7 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   for (int v = tid; v < D.n; v += nthr) {
     const int d = __ldcg(lab_ptr(D, v, p));
-    D.vst[p ^ 1][v].x = d;
+    *lab_ptr(D, v, p ^ 1) = d;
     const long long ad = __ldcg(add_ptr(D, v));
     if (ad) {
       *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
@@ -1106,8 +1108,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   // excess 0, no stamps.
   for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
   for (int v = tid; v < D.n; v += nthr) {
-    D.vst[0][v] = make_int2(0, -1);
-    D.vst[1][v] = make_int2(0, -1);
+    D.vs[v] = make_int4(0, -1, 0, -1);
     *exc_ptr(D, v) = 0;
     *add_ptr(D, v) = 0;
   }
