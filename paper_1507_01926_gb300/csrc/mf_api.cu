@@ -124,7 +124,7 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab, g->ea,
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab,
                 g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -167,9 +167,8 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
   if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
-  if ((rc = dalloc((void **)&g->vs, n * 16, "cudaMalloc vertex state"))) return rc;
+  if ((rc = dalloc((void **)&g->vs, n * sizeof(VRec), "cudaMalloc vertex state"))) return rc;
   if ((rc = dalloc((void **)&g->blab, n * 4, "cudaMalloc BFS labels"))) return rc;
-  if ((rc = dalloc((void **)&g->ea, n * 16, "cudaMalloc excess"))) return rc;
   for (int k = 0; k < 3; k++)
     if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
   if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
@@ -267,7 +266,6 @@ Dev make_dev(const mf_graph *g) {
   D.rr = g->rr;
   D.vs = g->vs;
   D.blab = g->blab;
-  D.ea = g->ea;
   for (int k = 0; k < 3; k++) D.list[k] = g->list[k];
   D.src = g->src;
   D.snk = g->snk;
@@ -595,7 +593,7 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }
   if (label) {
-    e = cudaMemcpy2DAsync(label, sizeof(int), g->vs, sizeof(int4), sizeof(int), n, cudaMemcpyDeviceToHost,
+    e = cudaMemcpy2DAsync(label, sizeof(int), g->vs, sizeof(VRec), sizeof(int), n, cudaMemcpyDeviceToHost,
                           g->stream);  // the label half of every slot-0 entry
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
@@ -603,7 +601,8 @@ int mf_run_rounds(mf_graph *g, int64_t rounds, int32_t final_relabel, int32_t *r
       if (label[v] > g->n) label[v] = g->n;
   }
   if (excess) {
-    e = cudaMemcpy2DAsync(excess, 8, g->ea, 16, 8, n, cudaMemcpyDeviceToHost, g->stream);  // excess halves
+    e = cudaMemcpy2DAsync(excess, 8, &g->vs->exc, sizeof(VRec), 8, n, cudaMemcpyDeviceToHost,
+                          g->stream);  // the excess of every record
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
   }

@@ -40,12 +40,21 @@ struct Ctl {
 // the kernel reads cnt as one int4 and gr_req as one int2
 static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0, "Ctl layout");
 
+// Per-vertex record (addedExcess: excess received while the vertex is in the
+// working set).
+struct __align__(32) VRec {
+  int lab0, stamp0, lab1, stamp1;
+  long long exc, added;
+};
+static_assert(sizeof(VRec) == 32, "one sector per vertex");
+
 // Device view of one (possibly multi-instance) graph.
 //
-// Vertex state: two slots by round parity, each {label, active-round stamp},
-// interleaved per vertex: vs[v] = {label 0, stamp 0, label 1, stamp 1}, so that
-// the slot a round reads and the slot it writes share one 32-byte sector (the
-// gather of a neighbour's label brings in the stamp a push then sets). Round r
+// Vertex state, one 32-byte sector per vertex (VRec): two slots by round
+// parity, each {label, active-round stamp}, and the excess pair {excess,
+// addedExcess}. The slot a round reads, the slot it writes and the excess a
+// push adds to share the sector that the gather of a neighbour's label
+// brings into L2. Round r
 // reads the label of every vertex from slot r & 1 and a discharged vertex
 // writes d' into slot (r + 1) & 1; a vertex is in the working set of round r
 // iff its stamp in slot r & 1 equals r. A BFS works on its own label array
@@ -60,10 +69,8 @@ struct Dev {
   const int *__restrict__ rev;   // m
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
-  int4 *vs;          // n: {label 0, stamp 0, label 1, stamp 1} (above)
+  VRec *vs;          // n vertex records (above)
   int *blab;         // n: BFS labels (dense, so that BFS gathers stay in L2); copied into both label slots by the rebuild
-  long long *ea;     // 2n: {excess, addedExcess} of v at 2v, 2v + 1 (addedExcess: excess received while
-                     // the vertex is in the working set)
   int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance

@@ -21,9 +21,8 @@ struct mf_graph {
   // device state
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
   int2 *rr = nullptr;
-  int4 *vs = nullptr;  // {label 0, stamp 0, label 1, stamp 1} per vertex
+  mf::VRec *vs = nullptr;      // per-vertex labels, stamps and excess
   int *blab = nullptr;
-  long long *ea = nullptr;     // {excess, addedExcess} per vertex
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
   int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)

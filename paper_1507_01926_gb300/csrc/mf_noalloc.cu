@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for n vertices and m slots (offsets from the start).
 struct Layout {
-  size_t ctl, flags, term, rr, vs, blab, ea, list0, list1, list2, total;
+  size_t ctl, flags, term, rr, vs, blab, list0, list1, list2, total;
 };
 
 Layout layout(long long n, long long m) {
@@ -53,11 +53,9 @@ Layout layout(long long n, long long m) {
   L.rr = o;
   o = align256(o + 8 * (size_t)m);
   L.vs = o;
-  o = align256(o + 16 * (size_t)n);
+  o = align256(o + sizeof(VRec) * (size_t)n);
   L.blab = o;
   o = align256(o + 4 * (size_t)n);
-  L.ea = o;
-  o = align256(o + 16 * (size_t)n);
   L.list0 = o;
   o = align256(o + 4 * (size_t)n);
   L.list1 = o;
@@ -207,9 +205,8 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.rev = d_rev;
   D.cap = d_cap;
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
-  D.vs = reinterpret_cast<int4 *>(base + L.vs);
+  D.vs = reinterpret_cast<VRec *>(base + L.vs);
   D.blab = reinterpret_cast<int *>(base + L.blab);
-  D.ea = reinterpret_cast<long long *>(base + L.ea);
   D.list[0] = reinterpret_cast<int *>(base + L.list0);
   D.list[1] = reinterpret_cast<int *>(base + L.list1);
   D.list[2] = reinterpret_cast<int *>(base + L.list2);

@@ -87,10 +87,10 @@ __device__ __forceinline__ int2 load_slot(const Dev &D, int p, int v) {
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.ncap ? __ldg(&D.ncap[v]) : D.n_cap; }
 
 // excess and addedExcess of v share one 16-byte entry
-__device__ __forceinline__ long long *exc_ptr(const Dev &D, int v) { return D.ea + 2 * (size_t)v; }
-__device__ __forceinline__ long long *add_ptr(const Dev &D, int v) { return D.ea + 2 * (size_t)v + 1; }
+__device__ __forceinline__ long long *exc_ptr(const Dev &D, int v) { return &D.vs[v].exc; }
+__device__ __forceinline__ long long *add_ptr(const Dev &D, int v) { return &D.vs[v].added; }
 __device__ __forceinline__ longlong2 load_ea(const Dev &D, int v) {
-  return __ldcg(reinterpret_cast<const longlong2 *>(D.ea) + v);
+  return __ldcg(reinterpret_cast<const longlong2 *>(&D.vs[v].exc));
 }
 
 __device__ __forceinline__ void set_err(const Dev &D, int code, int where) {
@@ -1108,9 +1108,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   // excess 0, no stamps.
   for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
   for (int v = tid; v < D.n; v += nthr) {
-    D.vs[v] = make_int4(0, -1, 0, -1);
-    *exc_ptr(D, v) = 0;
-    *add_ptr(D, v) = 0;
+    reinterpret_cast<int4 *>(D.vs + v)[0] = make_int4(0, -1, 0, -1);
+    reinterpret_cast<longlong2 *>(D.vs + v)[1] = make_longlong2(0, 0);
   }
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
@@ -1137,7 +1136,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   if (ok && D.mode == MODE_SOLVE) {
     if (tid == 0) D.ctl->t_preflow = gtimer();
     for (int k = tid; k < D.ninst; k += nthr) {
-      const long long val = __ldcg(&D.ea[2 * (size_t)D.snk[k]]);
+      const long long val = __ldcg(exc_ptr(D, D.snk[k]));
       if (D.out_value) D.out_value[k] = val;
       if (k == 0) D.ctl->value = val;
     }
