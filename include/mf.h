@@ -243,6 +243,40 @@ int mf_batch_get_stats(const mf_batch *b, mf_stats *out);
 void mf_batch_destroy(mf_batch *b);
 
 /*
+ * Autotuning (no counterpart in the paper, which fixes freq 0.5, alpha 6 and
+ * beta 12 for a CPU). mf_autotune times solves of g under candidate options
+ * and keeps the fastest: coordinate descent over gr_time_ratio {0, 1, 2, 4},
+ * gr_freq {0.25, 0.5, 1, 2}, bin_thread {2, 4, 8}, bin_warp {128, 1024, 8192},
+ * the launch shape (threads per CTA, CTAs per SM) {(256, 2), (512, 1),
+ * (128, 4), (256, 1)} and kernel_variant {0..3}, starting from g's current
+ * options; candidates that are invalid together or do not fit the GPU are
+ * skipped. A candidate's time is the median device time of spec->reps solves
+ * (maximum flow value only, no per-arc outputs); spec->sweeps passes over the
+ * coordinates at most (fewer when a pass changes nothing); no new candidate
+ * starts once the solves took spec->time_budget_ms (0 = no limit). spec may
+ * be NULL (3 reps, 1 sweep, no limit). Every candidate must reproduce the flow
+ * values of the starting options, else MF_ERR_INTERNAL. On success g keeps the
+ * best options; *best and *best_ms (nullable) receive them and their median
+ * time. A solve error of a candidate is returned as is (g keeps the best
+ * options found before it).
+ *
+ * mf_set_options replaces the options of an existing graph (validated, the
+ * launch shape recomputed; opt->device must be the graph's device).
+ * mf_batch_set_options and mf_batch_autotune do the same for a batch (the
+ * values of all its instances are checked).
+ */
+typedef struct mf_tune_spec {
+  int32_t reps;           /* solves per candidate, 1..99 */
+  int32_t sweeps;         /* passes over the coordinates, 1..9 */
+  double time_budget_ms;  /* device time after which no new candidate starts; 0 = no limit */
+} mf_tune_spec;
+
+int mf_set_options(mf_graph *g, const mf_options *opt);
+int mf_autotune(mf_graph *g, const mf_tune_spec *spec, mf_options *best, double *best_ms);
+int mf_batch_set_options(mf_batch *b, const mf_options *opt);
+int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, double *best_ms);
+
+/*
  * Serving with continuous batching. mf_service_create starts worker lanes on
  * opt->device (each lane: a host thread, a CUDA stream and a share of the
  * SMs). mf_submit copies the instance (host arrays, paired-slot CSR) and

@@ -1,0 +1,93 @@
+"""Cached autotuning of solver options (mf_autotune / mf_batch_autotune in include/mf.h).
+
+The search itself runs in libmf (coordinate descent over candidate relabel triggers, degree bins, launch
+shapes and register budgets, every candidate timed on the GPU and checked to reproduce the flow values).
+This module only keeps its choices: a JSON file maps a device name and a workload key to the chosen
+options and their median solve time, so that a workload family is tuned once per device and later runs
+start from the cached options.
+
+Cache layout::
+
+    {"<device name>": {"<workload key>": {"options": {<mf_options fields>}, "ms": <median solve ms>}}}
+"""
+from __future__ import annotations
+
+import json
+import os
+import tempfile
+
+from . import mf
+
+DEFAULT_CACHE = os.environ.get("MF_TUNE_CACHE",
+                               os.path.join(os.path.expanduser("~"), ".cache", "paper_1507_01926_gb300_tune.json"))
+
+
+def workload_key(family: str, n: int, m: int, count: int = 1) -> str:
+    """Key of a workload family and size class: sizes are rounded to powers of two, so that instances of one
+    family and similar size share their tuned options."""
+
+    def p2(x):
+        return max(int(x), 1).bit_length()
+
+    return f"{family}/n2^{p2(n)}/m2^{p2(m)}/x{p2(count)}"
+
+
+def device_name(device: int = 0) -> str:
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_name(device)
+    except Exception:
+        pass
+    return f"cuda:{device}"
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(data: dict, path: str = DEFAULT_CACHE) -> None:
+    """Writes the cache atomically (a temporary file renamed over the old one)."""
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".tune", suffix=".json")
+    with os.fdopen(fd, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(key: str, device: str, path: str = DEFAULT_CACHE):
+    """(Options, ms) cached for (device, key), or None."""
+    e = load_cache(path).get(device, {}).get(key)
+    if not e:
+        return None
+    return mf.options_from_dict(e["options"]), float(e["ms"])
+
+
+def store(key: str, device: str, options: mf.Options, ms: float, path: str = DEFAULT_CACHE) -> None:
+    data = load_cache(path)
+    data.setdefault(device, {})[key] = {"options": mf.options_to_dict(options), "ms": float(ms)}
+    save_cache(data, path)
+
+
+def tuned(target, key: str, path: str = DEFAULT_CACHE, reps: int = 3, sweeps: int = 1,
+          time_budget_ms: float = 0.0, device: int = 0, retune: bool = False):
+    """Options for `target` (an mf.Graph or mf.Batch) under workload `key`: the cached choice when there is
+    one (applied with set_options), else a fresh mf_autotune run whose result is cached. Returns
+    (Options, median ms, from_cache)."""
+    dev = device_name(device)
+    hit = None if retune else lookup(key, dev, path)
+    if hit is not None:
+        opts, ms = hit
+        opts.device = device
+        target.set_options(opts)
+        return opts, ms, True
+    opts, ms = target.autotune(reps=reps, sweeps=sweeps, time_budget_ms=time_budget_ms)
+    store(key, dev, opts, ms, path)
+    return opts, ms, False

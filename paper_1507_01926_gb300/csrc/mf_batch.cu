@@ -232,4 +232,16 @@ int mf_batch_get_stats(const mf_batch *b, mf_stats *out) {
 
 void mf_batch_destroy(mf_batch *b) { destroy_union(b); }
 
+int mf_batch_set_options(mf_batch *b, const mf_options *opt) {
+  clear_error();
+  if (!b || !b->g || !opt) return fail(MF_ERR_INVALID_ARG, "null batch or options");
+  return set_options(b->g, opt);
+}
+
+int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, double *best_ms) {
+  clear_error();
+  if (!b || !b->g) return fail(MF_ERR_INVALID_ARG, "null batch");
+  return autotune(b->g, spec, best, best_ms);
+}
+
 }  // extern "C"

@@ -50,4 +50,6 @@ int solver_variants();
 int solver_variant_max_threads(int variant);
 int solver_occupancy(int block_threads, int *blocks_per_sm, int variant);
 cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant);
+int set_options(mf_graph *g, const mf_options *o);
+int autotune(mf_graph *g, const mf_tune_spec *spec, mf_options *best, double *best_ms);
 }  // namespace mf

@@ -35,6 +35,10 @@ class Options(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32), ("simple_rounds", ctypes.c_int32)]
 
 
+class TuneSpec(ctypes.Structure):
+    _fields_ = [("reps", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("time_budget_ms", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("rounds_phase1", ctypes.c_int64), ("global_relabels", ctypes.c_int64),
                 ("bfs_levels", ctypes.c_int64), ("scans_discharge", ctypes.c_int64), ("scans_bfs", ctypes.c_int64),
@@ -69,7 +73,8 @@ _lib = None
 EXPORTS = ["mf_default_options", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
            "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
            "mf_solve_trace", "mf_destroy_graph", "mf_batch_create", "mf_batch_solve", "mf_batch_get_stats",
-           "mf_batch_destroy", "mf_service_create", "mf_submit", "mf_poll", "mf_wait", "mf_service_destroy"]
+           "mf_batch_destroy", "mf_service_create", "mf_submit", "mf_poll", "mf_wait", "mf_service_destroy",
+           "mf_set_options", "mf_autotune", "mf_batch_set_options", "mf_batch_autotune"]
 
 
 def lib():
@@ -108,6 +113,10 @@ def lib():
         L.mf_wait.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double)]
         L.mf_service_destroy.argtypes = [vp]
         L.mf_service_destroy.restype = None
+        for f in (L.mf_set_options, L.mf_batch_set_options):
+            f.argtypes = [vp, ctypes.POINTER(Options)]
+        for f in (L.mf_autotune, L.mf_batch_autotune):
+            f.argtypes = [vp, ctypes.POINTER(TuneSpec), ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -142,6 +151,27 @@ def default_options(**overrides) -> Options:
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def options_to_dict(o: Options) -> dict:
+    return {k: getattr(o, k) for k, _ in Options._fields_}
+
+
+def options_from_dict(d: dict) -> Options:
+    o = default_options()
+    for k, v in d.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _autotune(fn, h, reps, sweeps, time_budget_ms):
+    spec = TuneSpec(int(reps), int(sweeps), float(time_budget_ms))
+    best = Options()
+    ms = ctypes.c_double()
+    _check(fn(h, ctypes.byref(spec), ctypes.byref(best), ctypes.byref(ms)))
+    return best, float(ms.value)
 
 
 @dataclass
@@ -255,6 +285,13 @@ class Graph:
         _check(lib().mf_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
 
+    def set_options(self, options: Options):
+        _check(lib().mf_set_options(self._h, ctypes.byref(options)))
+
+    def autotune(self, reps: int = 3, sweeps: int = 1, time_budget_ms: float = 0.0):
+        """mf_autotune: times candidate options on this graph and keeps the fastest; returns (Options, median ms)."""
+        return _autotune(lib().mf_autotune, self._h, reps, sweeps, time_budget_ms)
+
     def run_rounds(self, rounds: int, final_relabel: bool = True):
         """Phase-1 state after `rounds` rounds: (residual int32[m], label int32[n], excess int64[n], rounds)."""
         res = np.zeros(self.m, np.int32)
@@ -337,6 +374,13 @@ class Batch:
         s = Stats()
         _check(lib().mf_batch_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+    def set_options(self, options: Options):
+        _check(lib().mf_batch_set_options(self._h, ctypes.byref(options)))
+
+    def autotune(self, reps: int = 3, sweeps: int = 1, time_budget_ms: float = 0.0):
+        """mf_batch_autotune: as Graph.autotune, checking the values of every instance."""
+        return _autotune(lib().mf_batch_autotune, self._h, reps, sweeps, time_budget_ms)
 
     def close(self):
         if self._h:
