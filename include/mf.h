@@ -100,6 +100,13 @@ typedef struct mf_options {
    * gr_time_ratio = 0 (forced in this mode) every solve of a graph gives the
    * same per-arc flow. More rounds than the default. */
   int32_t simple_rounds;
+  /* 1: capture a solve's launch sequence (control-block reset, the persistent
+   * kernel, the status read-back) into a CUDA graph on the first solve and
+   * replay it on later solves of the same graph with the same outputs (a
+   * changed output set, option or stream captures anew). Needs a stream
+   * other than the legacy default stream; on that stream the sequence is
+   * launched directly. mf_stats.solve_ms then times the whole replay. */
+  int32_t use_graph;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a

@@ -9,6 +9,11 @@ start from the cached options.
 Cache layout::
 
     {"<device name>": {"<workload key>": {"options": {<mf_options fields>}, "ms": <median solve ms>}}}
+
+A lookup that misses the user's cache falls back to ``tuned_gb300.json`` beside this module: the choices
+of the same search on a GB300 for the three standing workloads (the 256x256x128 3D grid, R-MAT scale 22 and
+the batch of 2048 layered graphs), written by ``python -m paper_1507_01926_gb300.autotune --out
+paper_1507_01926_gb300/tuned_gb300.json grid3d rmat layered``.
 """
 from __future__ import annotations
 
@@ -20,6 +25,7 @@ from . import mf
 
 DEFAULT_CACHE = os.environ.get("MF_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "paper_1507_01926_gb300_tune.json"))
+PACKAGED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
 
 
 def workload_key(family: str, n: int, m: int, count: int = 1) -> str:
@@ -62,9 +68,12 @@ def save_cache(data: dict, path: str = DEFAULT_CACHE) -> None:
     os.replace(tmp, path)
 
 
-def lookup(key: str, device: str, path: str = DEFAULT_CACHE):
-    """(Options, ms) cached for (device, key), or None."""
+def lookup(key: str, device: str, path: str = DEFAULT_CACHE, packaged: bool = True):
+    """(Options, ms) cached for (device, key) in `path`, else (packaged=True) in the packaged GB300 table,
+    else None."""
     e = load_cache(path).get(device, {}).get(key)
+    if not e and packaged:
+        e = load_cache(PACKAGED).get(device, {}).get(key)
     if not e:
         return None
     return mf.options_from_dict(e["options"]), float(e["ms"])
@@ -91,3 +100,54 @@ def tuned(target, key: str, path: str = DEFAULT_CACHE, reps: int = 3, sweeps: in
     opts, ms = target.autotune(reps=reps, sweeps=sweeps, time_budget_ms=time_budget_ms)
     store(key, dev, opts, ms, path)
     return opts, ms, False
+
+
+def _standing_workload(name: str):
+    """(key, target factory, note) of a standing workload: the 256x256x128 3D grid, R-MAT scale 22, or the
+    batch of 2048 layered graphs (tuned on its first 64 instances, stored under the full batch's key)."""
+    from . import inputs as I
+
+    if name == "layered":
+        params = I.config3_params()
+        n_all = m_all = 0
+        csrs, sts = [], []
+        for i, (L, W) in enumerate(params):
+            g = I.config3_instance(i, L, W)
+            c = mf.build_csr(g.n, g.tail, g.head, g.cap)
+            n_all, m_all = n_all + c.n, m_all + c.m
+            if i < 64:
+                c.arc_slot = None
+                csrs.append(c)
+                sts.append((g.s, g.t))
+        key = workload_key("layered", n_all, m_all, len(params))
+        return key, (lambda: mf.Batch(csrs, sts)), "first 64 of the 2048 layered graphs, mf_batch_autotune"
+    g = {"grid3d": I.config1, "rmat": I.config2}[name]()
+    c = mf.build_csr(g.n, g.tail, g.head, g.cap)
+    return workload_key(name, g.n, c.m), (lambda: mf.Graph.from_csr(c, g.s, g.t)), f"{g.name}, mf_autotune"
+
+
+def main(argv=None) -> int:
+    """Tunes the named standing workloads on cuda:0 and stores the choices (GPU required)."""
+    import argparse
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("workloads", nargs="+", choices=["grid3d", "rmat", "layered"])
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=2)
+    a = ap.parse_args(argv)
+    dev = device_name(0)
+    for name in a.workloads:
+        key, make, note = _standing_workload(name)
+        with make() as target:
+            opts, ms = target.autotune(reps=a.reps, sweeps=a.sweeps)
+        store(key, dev, opts, ms, a.out)
+        data = load_cache(a.out)
+        data[dev][key]["tuned_on"] = f"{note} reps={a.reps} sweeps={a.sweeps}"
+        save_cache(data, a.out)
+        print(json.dumps({"workload": name, "key": key, "ms": ms, "options": mf.options_to_dict(opts)}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -34,6 +34,11 @@ struct mf_graph {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // captured launch sequence (mf_options.use_graph) and what it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  mf::Dev gdev{};
+  cudaStream_t gstream = nullptr;
+  int ggrid = 0, gblock = 0, gvariant = -1;
 };
 
 namespace mf {

@@ -76,3 +76,20 @@ def test_tuning_entry_points_reject_null_arguments(built):
     assert L.mf_batch_set_options(None, ctypes.byref(o)) == -1
     assert L.mf_batch_autotune(None, None, None, None) == -1
     assert b"null" in L.mf_last_error()
+
+
+def test_packaged_table_is_a_fallback_of_valid_options(built, tmp_path):
+    from paper_1507_01926_gb300 import autotune as A
+    from paper_1507_01926_gb300 import mf
+
+    table = A.load_cache(A.PACKAGED)
+    assert "NVIDIA GB300" in table and len(table["NVIDIA GB300"]) == 3
+    for key, e in table["NVIDIA GB300"].items():
+        o = mf.options_from_dict(e["options"])  # every field is an mf_options field
+        assert o.block_threads % 32 == 0 and o.bin_warp >= o.bin_thread and e["ms"] > 0
+        empty = str(tmp_path / "none.json")
+        hit = A.lookup(key, "NVIDIA GB300", empty)
+        assert hit is not None and mf.options_to_dict(hit[0]) == mf.options_to_dict(o)
+        assert A.lookup(key, "NVIDIA GB300", empty, packaged=False) is None
+        assert A.lookup(key, "some other device", empty) is None
+    assert A.workload_key("grid3d", 8388610, 50331648) in table["NVIDIA GB300"]
