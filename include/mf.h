@@ -107,6 +107,19 @@ typedef struct mf_options {
    * other than the legacy default stream; on that stream the sequence is
    * launched directly. mf_stats.solve_ms then times the whole replay. */
   int32_t use_graph;
+  /* On graphs whose vertices other than s and t all have at most bin_thread
+   * slots, a CTA that adds at most K vertices to the next working set or BFS
+   * frontier keeps them in its shared memory and discharges or expands them
+   * itself in the next round or level, instead of appending them to the list
+   * in device memory (saves the list-space atomic, the list writes and the
+   * list reads of a round); a CTA with more appends them all, and appended
+   * entries are spread evenly over all CTAs. 0: off (always append);
+   * 1 (default): K = block_threads / 2; 32 <= K <= 512: that K, at most
+   * block_threads. While thread 0 of a CTA waits at the grid barrier before
+   * such a round or level, its other threads load the row offsets and arc
+   * heads of their kept vertices and pull the rest of their data into L2.
+   * No effect with simple_rounds. Results are the same for every setting. */
+  int32_t local_lists;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a

@@ -246,6 +246,8 @@ int check_options(const mf_options *o) {
   if (o->max_rounds < 0) return fail(MF_ERR_INVALID_ARG, "max_rounds must be >= 0");
   if (!(o->gr_time_ratio >= 0)) return fail(MF_ERR_INVALID_ARG, "gr_time_ratio must be >= 0");
   if (o->use_graph != 0 && o->use_graph != 1) return fail(MF_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
+    return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
     return fail(MF_ERR_INVALID_ARG, "kernel_variant must be in [0, %d)", solver_variants());
   if (o->block_threads > solver_variant_max_threads(o->kernel_variant))
@@ -281,6 +283,7 @@ Dev make_dev(const mf_graph *g) {
   D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
   D.simple = g->opt.simple_rounds ? 1 : 0;
   D.cta_vertices = g->max_degree > (long long)g->opt.bin_warp ? 1 : 0;
+  D.keep_local = keep_local_limit(g->opt, g->max_degree, g->block);
   D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
@@ -411,6 +414,7 @@ void mf_default_options(mf_options *o) {
   o->cut_only = 0;
   o->device = 0;
   o->gr_time_ratio = 2.0;
+  o->local_lists = 1;
 }
 
 const char *mf_last_error(void) { return last_error(); }

@@ -22,6 +22,7 @@ struct Ctl {
   int err;             // 0 or an MF_ERR_* code
   int err_where;       // which wait or check failed
   int cnt[4];          // list sizes of generations g % 4
+  int lcnt[4];         // entries of generation g % 4 kept in the CTAs' shared memory (all CTAs together)
   long long work[3];   // per-round relabel work, by round % 3
   int gr_req[2];       // time-based relabel request, by round parity
   long long value;     // flow value (excess of the sink after phase 1)
@@ -38,7 +39,8 @@ struct Ctl {
   int stopped_round;   // MODE_ROUNDS: rounds run
 };
 // the kernel reads cnt as one int4 and gr_req as one int2
-static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0, "Ctl layout");
+static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, lcnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0,
+              "Ctl layout");
 
 // Per-vertex record (addedExcess: excess received while the vertex is in the
 // working set).
@@ -91,6 +93,10 @@ struct Dev {
   int simple;              // 1: the simple synchronous rounds of Section 3 (push pass, then one relabel)
   int cta_vertices;        // 0: no vertex other than a source or sink has more than bin_warp slots, so no
                            //    discharge needs a whole CTA (the CTA-wide check is skipped)
+  int keep_local;          // a CTA that stages at most this many entries of a list generation keeps them in
+                           // its shared memory for the phase that consumes the generation instead of
+                           // appending them to the list in global memory (0: always append). Set only when
+                           // every vertex other than a source or sink is thread-sized (one thread per vertex)
   // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
   int2 *trace;
   long long trace_cap;

@@ -51,6 +51,7 @@ int launch_config(mf_graph *g);
 int check_options(const mf_options *o);
 Dev make_dev(const mf_graph *g);
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
+int keep_local_limit(const mf_options &o, long long max_degree, int block_threads);
 int solver_variants();
 int solver_variant_max_threads(int variant);
 int solver_occupancy(int block_threads, int *blocks_per_sm, int variant);

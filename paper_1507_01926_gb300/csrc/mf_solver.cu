@@ -170,6 +170,7 @@ constexpr int QCAP = 2048;  // per-CTA staging of list appends
 struct Snap {
   int err;
   int cnt[4];
+  int lcnt[4];
   long long work[3];
   int gr_req[2];
 };
@@ -181,14 +182,25 @@ struct Shared {
   int flag;
   int qn;                   // staged appends (may exceed QCAP; the excess went straight to the list)
   int qbase;
-  int qk;
+  int qk;                   // staged entries to publish to the list in global memory
+  int lk;                   // staged entries to keep in shared memory
   long long wsum;
   int imin[MAX_WARPS];
   long long lsum[MAX_WARPS];
+  int lqn[3];               // kept entries of list generation g, in lq[g % 3]
   int qbuf[QCAP];
+  int lq[3][MAX_BLOCK];
+  // read-only data of the vertex thread t handles first in the next round or
+  // BFS level, loaded while thread 0 waits at the grid barrier (pv[t] = -1:
+  // none). Row offsets and heads never change, so an entry is valid for its
+  // vertex whenever it is read.
+  int pv[MAX_BLOCK];
+  int pbeg[MAX_BLOCK];
+  int pdeg[MAX_BLOCK];
+  int phead[KT][MAX_BLOCK];
 };
 
-// Stages one append to the list of generation gen in shared memory; qflush
+// Stages one append to the list of generation gen in shared memory; phase_end
 // publishes the CTA's staged entries with one global atomic.
 __device__ __forceinline__ void qpush(const Dev &D, Shared &sh, int gen, int val) {
   const int i = atomicAdd(&sh.qn, 1);
@@ -208,17 +220,25 @@ __device__ __forceinline__ int sweep_chunk(int total) {
   return w < (int)blockDim.x ? w : (int)blockDim.x;
 }
 
-// All threads of the CTA call this at the end of a phase that appended to gen:
-// publishes the staged appends and adds the CTA's sum of `work` to *work_dst
-// (nullable) with two CTA barriers.
+// All threads of the CTA call this at the end of a phase that staged entries of
+// list generation gen, and adds the CTA's sum of `work` to *work_dst
+// (nullable). At most D.keep_local staged entries stay in the CTA's shared
+// memory (lq[gen % 3]; their number is added to lcnt), more are published to
+// the list in global memory with one atomic for the space. Every generation is
+// staged by exactly one phase. Two CTA barriers; the next phase starts after a
+// grid barrier, which begins with a CTA barrier.
 __device__ void phase_end(const Dev &D, Shared &sh, int gen, long long work, long long *work_dst) {
   const long long w = warp_sum(work);
   if ((threadIdx.x & 31) == 0 && w) atomicAdd(reinterpret_cast<unsigned long long *>(&sh.wsum), (unsigned long long)w);
   __syncthreads();
   if (threadIdx.x == 0) {
     const int k = min(sh.qn, QCAP);
-    sh.qk = k;
-    if (k > 0) sh.qbase = atomicAdd(&D.ctl->cnt[gen & 3], k);
+    const bool keep = sh.qn <= D.keep_local;  // keep_local <= MAX_BLOCK < QCAP: nothing overflowed
+    sh.qk = keep ? 0 : k;
+    sh.lk = keep ? k : 0;
+    sh.lqn[gen % 3] = keep ? k : 0;
+    if (!keep && k > 0) sh.qbase = atomicAdd(&D.ctl->cnt[gen & 3], k);
+    if (keep && k > 0) atomicAdd(&D.ctl->lcnt[gen & 3], k);
     if (work_dst && sh.wsum) atomic_add64(work_dst, sh.wsum);
     sh.qn = 0;
     sh.wsum = 0;
@@ -236,29 +256,8 @@ __device__ void phase_end(const Dev &D, Shared &sh, int gen, long long work, lon
         set_err(D, MF_ERR_INTERNAL, 11);
     }
   }
-  // the next phase starts after a grid barrier, which begins with a CTA barrier
-}
-
-// All threads of the CTA call this at the end of a phase that appended to gen.
-__device__ void qflush(const Dev &D, Shared &sh, int gen) {
-  __syncthreads();
-  const int k = min(sh.qn, QCAP);
-  if (k > 0) {
-    if (threadIdx.x == 0) sh.qbase = atomicAdd(&D.ctl->cnt[gen & 3], k);
-    __syncthreads();
-    const int base = sh.qbase;
-    int *L = list_of(D, gen);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      const int idx = base + i;
-      if (idx < D.n)
-        L[idx] = sh.qbuf[i];
-      else
-        set_err(D, MF_ERR_INTERNAL, 11);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) sh.qn = 0;
-  __syncthreads();
+  int *lq = sh.lq[gen % 3];
+  for (int i = threadIdx.x; i < sh.lk; i += blockDim.x) lq[i] = sh.qbuf[i];
 }
 
 // Block-wide sum of a 64-bit value (all threads call; result valid in all).
@@ -274,18 +273,75 @@ __device__ long long block_sum(long long x, Shared &sh) {
   return t;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// What the phase after a grid barrier is, for the prefetch in the barrier
+// window.
+enum PfKind : int { PF_NONE = 0, PF_ROUND = 1, PF_LEVEL = 2 };
+
+// Runs on every thread between its CTA's arrival at a grid barrier and the
+// barrier's completion. The next phase hands thread t its CTA's kept entry t
+// of generation `next` (a round: then entry t - n of the kept entries of
+// generation `prev`, prev >= 0, whose merge step it does): load that vertex's
+// row offsets and arc heads into shared memory (they never change) and pull
+// what the phase reads and updates (residual pairs, reverse-slot indices,
+// vertex records, neighbours' records or BFS labels) into L2. Loads of mutable
+// data would be stale, a prefetch into L2 is not.
+__device__ __forceinline__ void prefetch_next(const Dev &D, Shared &sh, int kind, int next, int prev) {
+  const int t = threadIdx.x;
+  sh.pv[t] = -1;
+  if (kind == PF_NONE) return;
+  const int nl = sh.lqn[next % 3];
+  if (t < nl) {
+    const int v = sh.lq[next % 3][t];
+    const int beg = __ldg(&D.row[v]);
+    const int deg = __ldg(&D.row[v + 1]) - beg;
+    if (deg > KT) return;
+    int h[KT];
+#pragma unroll
+    for (int i = 0; i < KT; i++) h[i] = i < deg ? __ldg(&D.head[beg + i]) : 0;
+    if (deg > 0) {
+      prefetch_l2(&D.rr[beg]);
+      prefetch_l2(&D.rr[beg + deg - 1]);
+    }
+    if (kind == PF_ROUND) {
+      prefetch_l2(&D.vs[v]);
+      if (deg > 0) {
+        prefetch_l2(&D.rev[beg]);
+        prefetch_l2(&D.rev[beg + deg - 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < KT; i++)
+        if (i < deg) prefetch_l2(&D.vs[h[i]]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < KT; i++)
+        if (i < deg) prefetch_l2(&D.blab[h[i]]);
+    }
+#pragma unroll
+    for (int i = 0; i < KT; i++) sh.phead[i][t] = h[i];
+    sh.pbeg[t] = beg;
+    sh.pdeg[t] = deg;
+    sh.pv[t] = v;
+  } else if (kind == PF_ROUND && prev >= 0 && t - nl < sh.lqn[prev % 3]) {
+    prefetch_l2(&D.vs[sh.lq[prev % 3][t - nl]]);
+  }
+}
+
 // Grid barrier on a monotone 64-bit arrival counter: CTA k's b-th arrival is
 // complete when the counter reaches b * gridDim.x. The CTA barrier orders the
 // CTA's writes before thread 0's release add, and thread 0's acquire load
-// before the CTA barrier that releases the other threads. Every wait is
-// bounded by D.timeout_ns; on expiry the error word is set and all CTAs leave
-// at their next barrier.
-__device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
+// before the CTA barrier that releases the other threads. While thread 0
+// waits, every thread runs the prefetch for the next phase (`pf`, see
+// prefetch_next). Every wait is bounded by D.timeout_ns; on expiry the error
+// word is set and all CTAs leave at their next barrier.
+__device__ bool grid_sync(const Dev &D, Shared &sh, int where, int pf = PF_NONE, int next = 0, int prev = -1) {
   __syncthreads();
+  unsigned long long *c = reinterpret_cast<unsigned long long *>(&D.ctl->bar);
+  if (threadIdx.x == 0) red_release_add64(c, 1ULL);
+  if (pf != PF_NONE) prefetch_next(D, sh, pf, next, prev);
   if (threadIdx.x == 0) {
-    unsigned long long *c = reinterpret_cast<unsigned long long *>(&D.ctl->bar);
     const unsigned long long target = (sh.bars + 1) * (unsigned long long)gridDim.x;
-    red_release_add64(c, 1ULL);
     if (ld_acquire64(c) < target) {
       const unsigned long long t0 = gtimer();
       unsigned spins = 0;
@@ -302,6 +358,7 @@ __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
     const Ctl *cw = D.ctl;
     const int err = vol_read(&cw->err);
     const int4 k = __ldcg(reinterpret_cast<const int4 *>(cw->cnt));
+    const int4 lk = __ldcg(reinterpret_cast<const int4 *>(cw->lcnt));
     const long long w0 = __ldcg(&cw->work[0]), w1 = __ldcg(&cw->work[1]), w2 = __ldcg(&cw->work[2]);
     const int2 q = __ldcg(reinterpret_cast<const int2 *>(cw->gr_req));
     sh.snap.err = err;
@@ -309,6 +366,10 @@ __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
     sh.snap.cnt[1] = k.y;
     sh.snap.cnt[2] = k.z;
     sh.snap.cnt[3] = k.w;
+    sh.snap.lcnt[0] = lk.x;
+    sh.snap.lcnt[1] = lk.y;
+    sh.snap.lcnt[2] = lk.z;
+    sh.snap.lcnt[3] = lk.w;
     sh.snap.work[0] = w0;
     sh.snap.work[1] = w1;
     sh.snap.work[2] = w2;
@@ -319,9 +380,69 @@ __device__ bool grid_sync(const Dev &D, Shared &sh, int where) {
   return sh.snap.err == 0;
 }
 
-// Size of the list of generation gen as of the last grid barrier.
+// Size of the list of generation gen in global memory as of the last grid
+// barrier.
 __device__ __forceinline__ int list_count(const Dev &D, const Shared &sh, int gen) {
   return min(sh.snap.cnt[gen & 3], D.n);
+}
+
+// Entries of generation gen in global memory and in all CTAs' shared memory.
+__device__ __forceinline__ long long gen_total(const Dev &D, const Shared &sh, int gen) {
+  return (long long)list_count(D, sh, gen) + sh.snap.lcnt[gen & 3];
+}
+
+// The items one CTA handles in a phase: its kept entries of up to two
+// generations (a, then b), then its share of the concatenation of two lists in
+// global memory (ga[0, na), then gb[0, nb)), spread over all CTAs in chunks of
+// `per` entries. Items are taken blockDim at a time; every thread of the CTA
+// runs the same number of sweeps.
+struct Sweep {
+  const int *la, *lb, *ga, *gb;
+  int nla, nlb, na, nb;
+  int per;     // global chunk size (0: no global entries)
+  int gitems;  // global items of this CTA (whole chunks; the last may run past na + nb)
+  int items;   // all items of this CTA
+};
+
+__device__ __forceinline__ Sweep make_sweep(const int *la, int nla, const int *lb, int nlb, const int *ga, int na,
+                                            const int *gb, int nb) {
+  Sweep w{la, lb, ga, gb, nla, nlb, na, nb, 0, 0, 0};
+  const int total = na + nb;
+  if (total > 0) {
+    w.per = sweep_chunk(total);
+    const int chunks = (total + w.per - 1) / w.per;
+    const int mine = (int)blockIdx.x < chunks ? (chunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    w.gitems = mine * w.per;
+  }
+  w.items = nla + nlb + w.gitems;
+  return w;
+}
+
+// Item `it` of the CTA: returns 1 (and the vertex) for an entry of the first
+// generation, 2 for one of the second, 0 for none.
+__device__ __forceinline__ int sweep_item(const Sweep &w, int it, int &v) {
+  if (it < w.nla) {
+    v = w.la[it];
+    return 1;
+  }
+  it -= w.nla;
+  if (it < w.nlb) {
+    v = w.lb[it];
+    return 2;
+  }
+  it -= w.nlb;
+  if (it >= w.gitems) return 0;
+  const int c = it / w.per;
+  const long long idx = ((long long)blockIdx.x + (long long)c * gridDim.x) * w.per + (it - c * w.per);
+  if (idx < w.na) {
+    v = __ldcg(&w.ga[idx]);
+    return 1;
+  }
+  if (idx < (long long)w.na + w.nb) {
+    v = __ldcg(&w.gb[idx - w.na]);
+    return 2;
+  }
+  return 0;
 }
 
 struct TStat {
@@ -373,36 +494,78 @@ __device__ __forceinline__ void flush_sink(const Dev &D, int sink, long long to_
   if (part.thread_rank() == 0) atomic_add64(exc_ptr(D, sink), sum);
 }
 
-// One thread, deg <= KT: arcs cached in registers for all passes.
-__device__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, int v, int beg, int deg, int dv,
-                                 int cap_v, TStat &st, long long &work) {
+// A vertex in the working set of round r whose label has reached the cap (it
+// was discovered while it relabeled to n): carry its label into the next slot
+// and fold its addedExcess into its excess.
+__device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int v, int dv) {
+  *lab_ptr(D, v, R.p ^ 1) = dv;
+  const long long ad = take_added(D, v);
+  if (ad) *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
+}
+
+// One thread, deg <= KT: arcs cached in registers for all passes. With
+// `pre`, the heads were loaded during the last grid barrier (prefetch_next)
+// and dv is not known yet: the vertex record, the residuals and all
+// neighbours' label slots are read in one round trip, then a vertex whose
+// label reached the cap is retired.
+__device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, int v, int beg,
+                                                 int deg, int dv, int cap_v, TStat &st, long long &work, bool pre) {
   int wv[KT], rs[KT], dw[KT], rv[KT];
   unsigned act = 0;
   // excess: own value plus what neighbours delivered so far; exactly that
   // delivered amount is taken out of addedExcess at the end (later deliveries stay)
   // (simple rounds: only the round-start excess; deliveries are folded in after the pushes)
-  const longlong2 ea = load_ea(D, v);
+  longlong2 ea;
+  if (pre) {
+    const int2 own = load_slot(D, R.p, v);
+    ea = load_ea(D, v);
+#pragma unroll
+    for (int i = 0; i < KT; i++) {
+      wv[i] = i < deg ? sh.phead[i][threadIdx.x] : 0;
+      rs[i] = 0;
+      dw[i] = 0;
+      rv[i] = 0;
+      if (i < deg) {
+        rs[i] = __ldcg(&D.rr[beg + i]).x;
+        rv[i] = __ldg(&D.rev[beg + i]);
+        const int2 x = load_slot(D, R.p, wv[i]);
+        dw[i] = x.x;
+        if (x.y == R.r) act |= 1u << i;
+      }
+    }
+    dv = own.x;
+    if (dv >= cap_v) {
+      retire_dead(D, R, v, dv);
+      return;
+    }
+    st.visits_dis++;
+#pragma unroll
+    for (int i = 0; i < KT; i++)
+      if (rs[i] <= 0) act &= ~(1u << i);
+  } else {
+    ea = load_ea(D, v);
+#pragma unroll
+    for (int i = 0; i < KT; i++) {
+      wv[i] = 0;
+      rs[i] = 0;
+      dw[i] = 0;
+      rv[i] = 0;
+      if (i < deg) {
+        wv[i] = __ldg(&D.head[beg + i]);
+        rs[i] = __ldcg(&D.rr[beg + i]).x;
+        rv[i] = __ldg(&D.rev[beg + i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KT; i++)
+      if (rs[i] > 0) {
+        const int2 x = load_slot(D, R.p, wv[i]);
+        dw[i] = x.x;
+        if (x.y == R.r) act |= 1u << i;
+      }
+  }
   const long long got = D.simple ? 0 : ea.y;
   long long ex = ea.x + got;
-#pragma unroll
-  for (int i = 0; i < KT; i++) {
-    wv[i] = 0;
-    rs[i] = 0;
-    dw[i] = 0;
-    rv[i] = 0;
-    if (i < deg) {
-      wv[i] = __ldg(&D.head[beg + i]);
-      rs[i] = __ldcg(&D.rr[beg + i]).x;
-      rv[i] = __ldg(&D.rev[beg + i]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < KT; i++)
-    if (rs[i] > 0) {
-      const int2 x = load_slot(D, R.p, wv[i]);
-      dw[i] = x.x;
-      if (x.y == R.r) act |= 1u << i;
-    }
   int dp = dv;
   long long to_sink = 0;
   int sink = -1;
@@ -630,14 +793,6 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
   __syncthreads();
 }
 
-// A vertex in the working set of round r whose label has reached the cap (it
-// was discovered while it relabeled to n): carry its label into the next slot
-// and fold its addedExcess into its excess.
-__device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int v, int dv) {
-  *lab_ptr(D, v, R.p ^ 1) = dv;
-  const long long ad = take_added(D, v);
-  if (ad) *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
-}
 
 // One round over a combined index space: entries [0, count) are the working
 // set of this round (list generation gen), discharged; entries [count, count +
@@ -650,21 +805,27 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
   const RoundCtx R{r, r & 1, gen + 1};
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
     D.ctl->work[(rnd + 1) % 3] = 0;
   }
-  const int *W = list_of(D, gen);
-  const int count = list_count(D, sh, gen);
-  const int *P = list_of(D, gen - 1);
-  const int cp = prev_valid ? list_count(D, sh, gen - 1) : 0;
-  const int total = count + cp;
+  // this round's working set (generation gen) and the previous one (gen - 1 = gen + 2 mod 3)
+  const Sweep sw = make_sweep(sh.lq[gen % 3], sh.lqn[gen % 3], sh.lq[(gen + 2) % 3], prev_valid ? sh.lqn[(gen + 2) % 3] : 0,
+                              list_of(D, gen), list_count(D, sh, gen), list_of(D, gen + 2),
+                              prev_valid ? list_count(D, sh, gen - 1) : 0);
   const int lane = threadIdx.x & 31;
   long long work = 0;
-  const int per = sweep_chunk(total);
-  for (int base = blockIdx.x * per; base < total; base += gridDim.x * per) {
-    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
+  for (int off = 0; off < sw.items; off += blockDim.x) {
+    int x = -1;
+    const int kind = sweep_item(sw, off + (int)threadIdx.x, x);
     int v = -1, beg = 0, deg = 0, cls = 0, dv = 0, cap_v = 0;
-    if (idx < count) {
-      v = __ldcg(&W[idx]);
+    if (kind == 1 && sh.pv[threadIdx.x] == x && sh.pdeg[threadIdx.x] <= D.bin_thread) {
+      v = x;  // thread-sized, row and heads loaded during the last grid barrier
+      cap_v = cap_of(D, v);
+      beg = sh.pbeg[threadIdx.x];
+      deg = sh.pdeg[threadIdx.x];
+      cls = 4;
+    } else if (kind == 1) {
+      v = x;
       dv = __ldcg(lab_ptr(D, v, R.p));
       cap_v = cap_of(D, v);
       if (dv >= cap_v) {
@@ -676,11 +837,11 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
         cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
         st.visits_dis++;
       }
-    } else if (idx < total) {
-      const int u = __ldcg(&P[idx - count]);
-      const int2 x = load_slot(D, R.p, u);
-      if (x.y != r) {  // not in this working set
-        *lab_ptr(D, u, R.p ^ 1) = x.x;
+    } else if (kind == 2) {
+      const int u = x;
+      const int2 y = load_slot(D, R.p, u);
+      if (y.y != r) {  // not in this working set
+        *lab_ptr(D, u, R.p ^ 1) = y.x;
         const long long ad = take_added(D, u);
         if (ad) atomic_add64(exc_ptr(D, u), ad);  // the excess of a non-member may receive pushes now
       }
@@ -712,7 +873,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       if (lane == leader) cls = 0;
       discharge_warp(D, sh, R, pv, pdv, pcap, st, work);
     }
-    if (cls == 1) discharge_thread(D, sh, R, v, beg, deg, dv, cap_v, st, work);
+    if (cls == 1 || cls == 4) discharge_thread(D, sh, R, v, beg, deg, dv, cap_v, st, work, cls == 4);
     __syncwarp();
   }
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -733,16 +894,15 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
 // set when it is below n. Vertices without excess keep their label.
 __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long long rnd, TStat &st) {
   const RoundCtx R{r, r & 1, gen + 1};
-  const int *W = list_of(D, gen);
-  const int count = list_count(D, sh, gen);
+  const Sweep sw = make_sweep(sh.lq[gen % 3], sh.lqn[gen % 3], nullptr, 0, list_of(D, gen), list_count(D, sh, gen),
+                              nullptr, 0);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   long long work = 0;
-  const int per = sweep_chunk(count);
-  for (int base = blockIdx.x * per; base < count; base += gridDim.x * per) {
-    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
+  for (int off = 0; off < sw.items; off += blockDim.x) {
+    int x = -1;
     int v = -1, beg = 0, deg = 0, cls = 0, cap_v = 0;
-    if (idx < count) {
-      v = __ldcg(&W[idx]);
+    if (sweep_item(sw, off + (int)threadIdx.x, x) == 1) {
+      v = x;
       const int dv = __ldcg(lab_ptr(D, v, R.p));
       cap_v = cap_of(D, v);
       // Section 3 step 4 for this vertex: the excess it received this round joins its excess now
@@ -832,16 +992,17 @@ __device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int lvl
   if (cf > 0 && atomicCAS(D.blab + w, UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
 }
 
-// One thread, deg <= KT, loads issued together.
+// One thread, deg <= KT, loads issued together (with `pre`, the heads were
+// loaded during the last grid barrier).
 __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, int deg, int lvl, bool reverse,
-                                           int next) {
+                                           int next, bool pre) {
   int w[KT], cf[KT], lab[KT];
 #pragma unroll
   for (int i = 0; i < KT; i++) {
     w[i] = 0;
     cf[i] = 0;
     if (i < deg) {
-      w[i] = __ldg(&D.head[beg + i]);
+      w[i] = pre ? sh.phead[i][threadIdx.x] : __ldg(&D.head[beg + i]);
       const int2 x = __ldcg(&D.rr[beg + i]);
       cf[i] = reverse ? x.y : x.x;
     }
@@ -855,19 +1016,27 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
 }
 
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
-  const int *F = list_of(D, gen);
   const int next = gen + 1;
-  const int count = list_count(D, sh, gen);
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
+  const Sweep sw = make_sweep(sh.lq[gen % 3], sh.lqn[gen % 3], nullptr, 0, list_of(D, gen), list_count(D, sh, gen),
+                              nullptr, 0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
+  }
   const int lane = threadIdx.x & 31;
-  const int per = sweep_chunk(count);
-  for (int base = blockIdx.x * per; base < count; base += gridDim.x * per) {
-    const int idx = (int)threadIdx.x < per ? base + threadIdx.x : INT_MAX;
-    const int v = idx < count ? __ldcg(&F[idx]) : -1;
+  for (int off = 0; off < sw.items; off += blockDim.x) {
+    int v = -1;
+    if (sweep_item(sw, off + (int)threadIdx.x, v) != 1) v = -1;
     int beg = 0, deg = 0, cls = 0;
+    const bool pre = v >= 0 && sh.pv[threadIdx.x] == v;  // row and heads loaded during the last grid barrier
     if (v >= 0) {
-      beg = __ldg(&D.row[v]);
-      deg = __ldg(&D.row[v + 1]) - beg;
+      if (pre) {
+        beg = sh.pbeg[threadIdx.x];
+        deg = sh.pdeg[threadIdx.x];
+      } else {
+        beg = __ldg(&D.row[v]);
+        deg = __ldg(&D.row[v + 1]) - beg;
+      }
       cls = deg <= KT ? 1 : (deg <= D.bin_warp ? 2 : 3);
       st.scans_bfs += deg;
       st.visits_bfs++;
@@ -894,7 +1063,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, lvl, reverse, next);
       __syncwarp();
     }
-    if (cls == 1) bfs_thread(D, sh, beg, deg, lvl, reverse, next);
+    if (cls == 1) bfs_thread(D, sh, beg, deg, lvl, reverse, next, pre);
     __syncwarp();
   }
   phase_end(D, sh, next, 0, nullptr);
@@ -909,7 +1078,10 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   const int next = gen + 1;
   // phase A: every label to UNV (excess-holding non-terminals become seeds)
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.ctl->cnt[(gen + 2) & 3] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
+  }
   for (int v = tid; v < D.n; v += nthr) {
     int x = UNV;
     if (excess_seeds) {
@@ -921,7 +1093,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     }
     D.blab[v] = x;
   }
-  qflush(D, sh, next);
+  phase_end(D, sh, next, 0, nullptr);
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
@@ -934,16 +1106,16 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   for (int lvl = 0;; lvl++) {
-    const int fcount = list_count(D, sh, gen);
+    const long long fcount = gen_total(D, sh, gen);
     if (fcount == 0) break;
     if (timer && D.trace_lv) {
       const long long k = D.ctl->levels;
-      if (k < D.trace_lv_cap) D.trace_lv[k] = fcount;
+      if (k < D.trace_lv_cap) D.trace_lv[k] = (int)fcount;
     }
     const unsigned long long t0 = timer ? gtimer() : 0;
     bfs_level(D, sh, gen, lvl, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
-    if (!grid_sync(D, sh, where)) return false;
+    if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
     gen++;
     if (timer) {
       D.ctl->levels++;
@@ -967,6 +1139,7 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
   const int p = r & 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
     D.ctl->grs++;
   }
   for (int v = tid; v < D.n; v += nthr) {
@@ -988,8 +1161,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
       qpush(D, sh, next, v);
     }
   }
-  qflush(D, sh, next);
-  if (!grid_sync(D, sh, 3)) return false;
+  phase_end(D, sh, next, 0, nullptr);
+  if (!grid_sync(D, sh, 3, PF_ROUND, next)) return false;
   gen++;
   return true;
 }
@@ -1034,7 +1207,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       time_req = false;
       prev_valid = false;
     }
-    const int count = list_count(D, sh, gen);
+    const long long count = gen_total(D, sh, gen);
     if (count == 0) {
       if (fresh) break;
       since_gr = LLONG_MAX;
@@ -1048,7 +1221,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     unsigned long long t0 = 0;
     if (timer) {
       D.ctl->rounds_by_size[count < 1024 ? 0 : count < 16384 ? 1 : count < 262144 ? 2 : 3]++;
-      if (D.trace && rnd < D.trace_cap) D.trace[rnd] = make_int2(count, fresh ? 1 : 0);
+      if (D.trace && rnd < D.trace_cap) D.trace[rnd] = make_int2((int)count, fresh ? 1 : 0);
       t0 = gtimer();
       D.ctl->gr_req[rnd & 1] =
           D.gr_time_ratio > 0 && (double)(t0 - last_gr_end) > D.gr_time_ratio * (double)last_gr_ns;
@@ -1056,7 +1229,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     fresh = false;
     unsigned long long tp = t0;
     round_phase(D, sh, r, gen, prev_valid, rnd, st, tp);
-    if (!grid_sync(D, sh, 4)) return false;
+    if (!grid_sync(D, sh, 4, D.simple ? PF_NONE : PF_ROUND, gen + 1, gen)) return false;
     if (D.simple) {
       relabel_phase(D, sh, r, gen, rnd, st);
       if (!grid_sync(D, sh, 4)) return false;
@@ -1098,7 +1271,9 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
     sh.bars = 0;
     sh.qn = 0;
     sh.wsum = 0;
+    sh.lqn[0] = sh.lqn[1] = sh.lqn[2] = 0;
   }
+  sh.pv[threadIdx.x] = -1;
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   TStat st;
@@ -1225,6 +1400,13 @@ int solver_variants() { return NUM_VARIANTS; }
 
 int solver_variant_max_threads(int variant) {
   return variant >= 0 && variant < NUM_VARIANTS ? kVariants[variant].max_threads : 0;
+}
+
+int keep_local_limit(const mf_options &o, long long max_degree, int block_threads) {
+  if (!o.local_lists || o.simple_rounds) return 0;
+  if (max_degree > o.bin_thread || max_degree > KT) return 0;  // not every vertex is thread-sized
+  const int k = o.local_lists == 1 ? block_threads / 2 : o.local_lists;
+  return k < block_threads ? k : block_threads;  // block_threads <= MAX_BLOCK
 }
 
 int solver_occupancy(int block_threads, int *blocks_per_sm, int variant) {
