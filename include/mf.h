@@ -120,6 +120,12 @@ typedef struct mf_options {
    * heads of their kept vertices and pull the rest of their data into L2.
    * No effect with simple_rounds. Results are the same for every setting. */
   int32_t local_lists;
+  /* Global relabels and cut BFS: with local_lists active, a CTA expands the
+   * vertices it reached itself for up to bfs_hops levels per grid barrier
+   * (label-correcting: a label found too early is lowered later; the labels
+   * at the end are the exact BFS distances either way). 1: one level per
+   * barrier, as Algorithm 2. Default 8; range [1, 64]. */
+  int32_t bfs_hops;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
@@ -334,7 +340,7 @@ void mf_service_destroy(mf_service *svc);
  * enqueued on `stream` (a cudaStream_t); the call returns when the solve is
  * done. All working state lives in one static device scratch area of 32 MiB
  * that every GPU loading the library holds until the process exits; a graph
- * needing more (about 52 bytes per vertex + 8 per slot) is rejected with
+ * needing more (about 56 bytes per vertex + 8 per slot) is rejected with
  * MF_ERR_TOO_LARGE before any work. The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine. The first call on each device looks
  * up the scratch area's device address (cudaGetSymbolAddress); make that first

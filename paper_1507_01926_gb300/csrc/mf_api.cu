@@ -169,7 +169,7 @@ int alloc_state(mf_graph *g) {
   if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
   if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
   if ((rc = dalloc((void **)&g->vs, n * sizeof(VRec), "cudaMalloc vertex state"))) return rc;
-  if ((rc = dalloc((void **)&g->blab, n * 4, "cudaMalloc BFS labels"))) return rc;
+  if ((rc = dalloc((void **)&g->blab, n * 8, "cudaMalloc BFS labels"))) return rc;
   for (int k = 0; k < 3; k++)
     if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
   if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
@@ -246,6 +246,7 @@ int check_options(const mf_options *o) {
   if (o->max_rounds < 0) return fail(MF_ERR_INVALID_ARG, "max_rounds must be >= 0");
   if (!(o->gr_time_ratio >= 0)) return fail(MF_ERR_INVALID_ARG, "gr_time_ratio must be >= 0");
   if (o->use_graph != 0 && o->use_graph != 1) return fail(MF_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (o->bfs_hops < 1 || o->bfs_hops > 64) return fail(MF_ERR_INVALID_ARG, "bfs_hops must be in [1, 64]");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
@@ -284,6 +285,7 @@ Dev make_dev(const mf_graph *g) {
   D.simple = g->opt.simple_rounds ? 1 : 0;
   D.cta_vertices = g->max_degree > (long long)g->opt.bin_warp ? 1 : 0;
   D.keep_local = keep_local_limit(g->opt, g->max_degree, g->block);
+  D.bfs_hops = D.keep_local > 0 ? g->opt.bfs_hops : 1;
   D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
@@ -415,6 +417,7 @@ void mf_default_options(mf_options *o) {
   o->device = 0;
   o->gr_time_ratio = 2.0;
   o->local_lists = 1;
+  o->bfs_hops = 8;
 }
 
 const char *mf_last_error(void) { return last_error(); }

@@ -72,7 +72,9 @@ struct Dev {
   const int *__restrict__ cap;   // m, input capacities (= initial residuals)
   int2 *rr;          // m: {residual of the slot, residual of its reverse slot}
   VRec *vs;          // n vertex records (above)
-  int *blab;         // n: BFS labels (dense, so that BFS gathers stay in L2); copied into both label slots by the rebuild
+  unsigned long long *blab;  // n: BFS words {label, flags} (dense, so that BFS gathers stay in L2); the rebuild
+                             // copies the labels into both label slots
+  int bfs_hops;      // BFS levels a CTA may expand per grid barrier (1: one level per barrier)
   int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance

@@ -22,7 +22,7 @@ struct mf_graph {
   int *row = nullptr, *head = nullptr, *rev = nullptr, *cap = nullptr;
   int2 *rr = nullptr;
   mf::VRec *vs = nullptr;      // per-vertex labels, stamps and excess
-  int *blab = nullptr;
+  unsigned long long *blab = nullptr;
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
   int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)

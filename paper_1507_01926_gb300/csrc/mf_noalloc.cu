@@ -55,7 +55,7 @@ Layout layout(long long n, long long m) {
   L.vs = o;
   o = align256(o + sizeof(VRec) * (size_t)n);
   L.blab = o;
-  o = align256(o + 4 * (size_t)n);
+  o = align256(o + 8 * (size_t)n);
   L.list0 = o;
   o = align256(o + 4 * (size_t)n);
   L.list1 = o;
@@ -155,7 +155,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   const Layout L = layout(n, m);
   if (L.total > NOALLOC_SCRATCH_BYTES)
     return fail(MF_ERR_TOO_LARGE,
-                "graph needs %zu bytes of scratch (about 52 per vertex + 8 per slot); the fixed area holds %zu",
+                "graph needs %zu bytes of scratch (about 56 per vertex + 8 per slot); the fixed area holds %zu",
                 L.total, NOALLOC_SCRATCH_BYTES);
   unsigned char *base = nullptr;
   int rc = scratch_base(&base);
@@ -206,7 +206,8 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.cap = d_cap;
   D.rr = reinterpret_cast<int2 *>(base + L.rr);
   D.vs = reinterpret_cast<VRec *>(base + L.vs);
-  D.blab = reinterpret_cast<int *>(base + L.blab);
+  D.blab = reinterpret_cast<unsigned long long *>(base + L.blab);
+  D.bfs_hops = 1;
   D.list[0] = reinterpret_cast<int *>(base + L.list0);
   D.list[1] = reinterpret_cast<int *>(base + L.list1);
   D.list[2] = reinterpret_cast<int *>(base + L.list2);

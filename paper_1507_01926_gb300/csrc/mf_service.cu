@@ -48,7 +48,7 @@ struct Request {
 
 // Device bytes one request occupies while resident (vertex state, slot
 // arrays, staging during creation, outputs).
-size_t footprint(long long n, long long m) { return (size_t)(61 * n + 32 * m + 65536); }
+size_t footprint(long long n, long long m) { return (size_t)(65 * n + 32 * m + 65536); }
 
 }  // namespace
 

@@ -189,6 +189,8 @@ struct Shared {
   long long lsum[MAX_WARPS];
   int lqn[3];               // kept entries of list generation g, in lq[g % 3]
   int qbuf[QCAP];
+  int qrow[MAX_BLOCK];      // BFS staging: row[v] of qbuf[i] (i < MAX_BLOCK) when known (qdeg[i] >= 0)
+  int qdeg[MAX_BLOCK];      // BFS staging: degree of qbuf[i] (i < MAX_BLOCK), -1 when unknown
   int lq[3][MAX_BLOCK];
   // read-only data of the vertex thread t handles first in the next round or
   // BFS level, loaded while thread 0 waits at the grid barrier (pv[t] = -1:
@@ -204,10 +206,27 @@ struct Shared {
 // publishes the CTA's staged entries with one global atomic.
 __device__ __forceinline__ void qpush(const Dev &D, Shared &sh, int gen, int val) {
   const int i = atomicAdd(&sh.qn, 1);
-  if (i < QCAP)
+  if (i < QCAP) {
     sh.qbuf[i] = val;
-  else
+    if (i < MAX_BLOCK) sh.qdeg[i] = -1;
+  } else {
     append(D, gen, val);
+  }
+}
+
+// qpush with the row offsets of the staged vertex (BFS: read while the vertex
+// was offered its label, so that an expansion inside the CTA starts at its arcs).
+__device__ __forceinline__ void qpush_row(const Dev &D, Shared &sh, int gen, int val, int beg, int deg) {
+  const int i = atomicAdd(&sh.qn, 1);
+  if (i < QCAP) {
+    sh.qbuf[i] = val;
+    if (i < MAX_BLOCK) {
+      sh.qrow[i] = beg;
+      sh.qdeg[i] = deg;
+    }
+  } else {
+    append(D, gen, val);
+  }
 }
 
 // Entries of a list that one CTA takes per sweep: a whole block when the list
@@ -979,24 +998,57 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
 
 // ------------------------------------------------------------------ BFS
 //
-// Level-synchronous BFS (Algorithm 2) on label slot 0. A frontier vertex v at
-// level k discovers w through slot a = (v -> w) when the tested residual is
-// positive (reverse BFS for the global relabel: res[rev[a]] = c_f(w, v);
-// forward BFS for the cut: res[a] = c_f(v, w)) and CAS(label(w): UNV -> k + 1)
-// succeeds.
+// BFS (Algorithm 2) from the seeds, on 64-bit words blab[v] = {label (high
+// half), flags (low half)}: bit 0 = v is queued for expansion, bit 1 = v is a
+// blocker (never entered). A queued vertex v is expanded with its current
+// label l, read while its queued bit is cleared (one atomic); through slot
+// a = (v -> w) it offers w the label l + 1 when the tested residual is positive
+// (reverse BFS for the global relabel: res[rev[a]] = c_f(w, v); forward BFS
+// for the cut: res[a] = c_f(v, w)) with atomicMin(blab[w], {l + 1, queued}).
+// The offer lowers w's label iff l + 1 is smaller; w joins the next list iff
+// it was not queued already (a queued w is expanded later with its newest
+// label). Expanding the list level by level with a grid barrier between
+// levels gives every vertex its BFS distance the first time, as Algorithm 2
+// does. With D.bfs_hops > 1 a CTA also expands the few vertices it reached
+// itself right away, up to bfs_hops levels per grid barrier: a label found
+// that way can be too large and is lowered by a later offer, which queues the
+// vertex again. Either way the words settle when no vertex is queued, and then
+// every label is the exact distance: each label is the length of a path, and
+// every arc out of an expanded vertex was offered with that vertex's final
+// label.
 
-__device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int lvl, bool reverse, int next) {
+constexpr unsigned long long BQ = 1ULL;  // queued
+constexpr unsigned long long BB = 2ULL;  // blocker
+
+__device__ __forceinline__ unsigned long long bword(int label, unsigned long long flags) {
+  return ((unsigned long long)(unsigned)label << 32) | flags;
+}
+
+// Expansion start: clears v's queued bit and returns its label.
+__device__ __forceinline__ int bfs_take(const Dev &D, int v) {
+  return (int)(atomicAnd(D.blab + v, ~BQ) >> 32);
+}
+
+// Offers label l to w; true when w must join the next list.
+__device__ __forceinline__ bool bfs_offer(const Dev &D, int w, int l) {
+  const unsigned long long c = bword(l, BQ);
+  const unsigned long long old = atomicMin(D.blab + w, c);
+  return old > c && !(old & BQ);
+}
+
+__device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int l, bool reverse, int next) {
   const int w = __ldg(&D.head[a]);
   const int2 x = __ldcg(&D.rr[a]);
   const int cf = reverse ? x.y : x.x;
-  if (cf > 0 && atomicCAS(D.blab + w, UNV, lvl + 1) == UNV) qpush(D, sh, next, w);
+  if (cf > 0 && bfs_offer(D, w, l)) qpush(D, sh, next, w);
 }
 
 // One thread, deg <= KT, loads issued together (with `pre`, the heads were
 // loaded during the last grid barrier).
-__device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, int deg, int lvl, bool reverse,
-                                           int next, bool pre) {
-  int w[KT], cf[KT], lab[KT];
+__device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, int deg, int l, bool reverse, int next,
+                                           bool pre) {
+  int w[KT], cf[KT];
+  bool got[KT];
 #pragma unroll
   for (int i = 0; i < KT; i++) {
     w[i] = 0;
@@ -1007,15 +1059,32 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
       cf[i] = reverse ? x.y : x.x;
     }
   }
-  // all CAS first (in flight together), then the appends
+  if (D.bfs_hops > 1) {
+    // all offers and the offered vertices' row offsets in flight together
+    int rb[KT], re[KT];
 #pragma unroll
-  for (int i = 0; i < KT; i++) lab[i] = cf[i] > 0 ? atomicCAS(D.blab + w[i], UNV, lvl + 1) : 0;
+    for (int i = 0; i < KT; i++) {
+      got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
+      rb[i] = cf[i] > 0 ? __ldg(&D.row[w[i]]) : 0;
+      re[i] = cf[i] > 0 ? __ldg(&D.row[w[i] + 1]) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < KT; i++)
+      if (got[i]) qpush_row(D, sh, next, w[i], rb[i], re[i] - rb[i]);
+    return;
+  }
+  // all offers first (in flight together), then the appends
+#pragma unroll
+  for (int i = 0; i < KT; i++) got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
 #pragma unroll
   for (int i = 0; i < KT; i++)
-    if (cf[i] > 0 && lab[i] == UNV) qpush(D, sh, next, w[i]);
+    if (got[i]) qpush(D, sh, next, w[i]);
 }
 
-__device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool reverse, TStat &st) {
+// One BFS level: expands the list of generation gen into generation gen + 1,
+// then (D.bfs_hops > 1) up to bfs_hops - 1 more levels of the vertices this
+// CTA reached itself, while they fit one per thread.
+__device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat &st) {
   const int next = gen + 1;
   const Sweep sw = make_sweep(sh.lq[gen % 3], sh.lqn[gen % 3], nullptr, 0, list_of(D, gen), list_count(D, sh, gen),
                               nullptr, 0);
@@ -1027,9 +1096,10 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
   for (int off = 0; off < sw.items; off += blockDim.x) {
     int v = -1;
     if (sweep_item(sw, off + (int)threadIdx.x, v) != 1) v = -1;
-    int beg = 0, deg = 0, cls = 0;
+    int beg = 0, deg = 0, cls = 0, l = 0;
     const bool pre = v >= 0 && sh.pv[threadIdx.x] == v;  // row and heads loaded during the last grid barrier
     if (v >= 0) {
+      l = bfs_take(D, v) + 1;
       if (pre) {
         beg = sh.pbeg[threadIdx.x];
         deg = sh.pdeg[threadIdx.x];
@@ -1044,13 +1114,19 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
     for (bool any = __syncthreads_or(cls == 3); any;) {
       if (threadIdx.x == 0) sh.pick = -1;
       __syncthreads();
-      if (cls == 3) sh.pick = v;
+      if (cls == 3) sh.pick = threadIdx.x;
       __syncthreads();
-      const int pv = sh.pick;
-      if (pv < 0) break;
-      if (v == pv) cls = 0;
+      const int pt = sh.pick;
+      if (pt < 0) break;
+      if (threadIdx.x == pt) {
+        cls = 0;
+        sh.imin[0] = v;
+        sh.imin[1] = l;
+      }
+      __syncthreads();
+      const int pv = sh.imin[0], pl = sh.imin[1];
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, sh, a, lvl, reverse, next);
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, sh, a, pl, reverse, next);
       __syncthreads();
     }
     for (;;) {
@@ -1058,21 +1134,49 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, int lvl, bool rever
       if (!mm) break;
       const int leader = __ffs(mm) - 1;
       const int pv = __shfl_sync(FULL, v, leader);
+      const int pl = __shfl_sync(FULL, l, leader);
       if (lane == leader) cls = 0;
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
-      for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, lvl, reverse, next);
+      for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, pl, reverse, next);
       __syncwarp();
     }
-    if (cls == 1) bfs_thread(D, sh, beg, deg, lvl, reverse, next, pre);
+    if (cls == 1) bfs_thread(D, sh, beg, deg, l, reverse, next, pre);
     __syncwarp();
+  }
+  // more levels inside the CTA (only on graphs whose vertices are all
+  // thread-sized; staged entries are taken out of the staging buffer)
+  for (int hop = 1; hop < D.bfs_hops; hop++) {
+    __syncthreads();  // staging of the previous level complete
+    const int k = sh.qn;
+    if (k == 0 || k > (int)blockDim.x) break;
+    const int v = (int)threadIdx.x < k ? sh.qbuf[threadIdx.x] : -1;
+    int beg = v >= 0 ? sh.qrow[threadIdx.x] : 0;
+    int deg = v >= 0 ? sh.qdeg[threadIdx.x] : 0;
+    __syncthreads();  // every thread has read qn and its entry
+    if (threadIdx.x == 0) sh.qn = 0;
+    __syncthreads();
+    if (v >= 0) {
+      if (deg < 0) {
+        beg = __ldg(&D.row[v]);
+        deg = __ldg(&D.row[v + 1]) - beg;
+      }
+      if (deg > KT) {
+        qpush(D, sh, next, v);  // still queued: the next level's sweep expands it
+      } else {
+        const int l = bfs_take(D, v) + 1;
+        st.scans_bfs += deg;
+        st.visits_bfs++;
+        bfs_thread(D, sh, beg, deg, l, reverse, next, false);
+      }
+    }
   }
   phase_end(D, sh, next, 0, nullptr);
 }
 
-// BFS from `seeds` (label 0) on label slot 0. `blockers` get UNV + 1 and are
-// never reached. With `excess_seeds`, every vertex holding excess whose label
-// lies in [1, cap] is a seed as well (cut from the maximum preflow). Returns
-// false on error. On return the last list generation (gen) is empty.
+// BFS from `seeds` (label 0) over blab. `blockers` are never entered. With
+// `excess_seeds`, every vertex holding excess whose label lies in [1, cap] is
+// a seed as well (cut from the maximum preflow). Returns false on error. On
+// return the last list generation (gen) is empty and no vertex is queued.
 __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *blockers, int nterm, bool reverse,
                     bool excess_seeds, int &gen, TStat &st, int where) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -1083,11 +1187,11 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     D.ctl->lcnt[(gen + 2) & 3] = 0;
   }
   for (int v = tid; v < D.n; v += nthr) {
-    int x = UNV;
+    unsigned long long x = bword(UNV, 0);
     if (excess_seeds) {
       const int d = __ldcg(lab_ptr(D, v, 0));
       if (d >= 1 && d <= cap_of(D, v) && __ldcg(exc_ptr(D, v)) > 0) {
-        x = 0;
+        x = bword(0, BQ);
         qpush(D, sh, next, v);
       }
     }
@@ -1097,15 +1201,15 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
-    D.blab[seeds[i]] = 0;
-    if (blockers) D.blab[blockers[i]] = UNV + 1;
+    D.blab[seeds[i]] = bword(0, BQ);
+    if (blockers) D.blab[blockers[i]] = bword(0, BB);
   }
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nterm; i += blockDim.x) append(D, next, seeds[i]);
   if (!grid_sync(D, sh, where)) return false;
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-  for (int lvl = 0;; lvl++) {
+  for (;;) {
     const long long fcount = gen_total(D, sh, gen);
     if (fcount == 0) break;
     if (timer && D.trace_lv) {
@@ -1113,7 +1217,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
       if (k < D.trace_lv_cap) D.trace_lv[k] = (int)fcount;
     }
     const unsigned long long t0 = timer ? gtimer() : 0;
-    bfs_level(D, sh, gen, lvl, reverse, st);
+    bfs_level(D, sh, gen, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
     if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
     gen++;
@@ -1124,6 +1228,14 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     }
   }
   return true;
+}
+
+// Label of v after a BFS: its distance, cap for an unreached vertex, cap + 1
+// for a blocker.
+__device__ __forceinline__ int bfs_label(unsigned long long x, int cap) {
+  if (x & BB) return cap + 1;
+  const int l = (int)(x >> 32);
+  return l >= UNV ? cap : l;
 }
 
 // Global relabel (Algorithm 2 from the sinks, never entering the sources),
@@ -1143,9 +1255,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     D.ctl->grs++;
   }
   for (int v = tid; v < D.n; v += nthr) {
-    const int x = __ldcg(D.blab + v);
     const int c = cap_of(D, v);
-    const int d = x == UNV ? c : (x == UNV + 1 ? c + 1 : x);
+    const int d = bfs_label(__ldcg(D.blab + v), c);
     *lab_ptr(D, v, 0) = d;
     *lab_ptr(D, v, 1) = d;
     const longlong2 ea = load_ea(D, v);
@@ -1345,7 +1456,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
           unsigned bits = 0;
           for (int j = 0; j < 32; j++) {
             const int v = wd * 32 + j;
-            if (v < D.n && __ldcg(D.blab + v) != UNV) bits |= 1u << j;
+            if (v < D.n && (int)(__ldcg(D.blab + v) >> 32) != UNV) bits |= 1u << j;
           }
           D.out_cut[wd] = bits;
         }
