@@ -149,7 +149,7 @@ def sized_oracle_run(g, seconds: float):
         r = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False, want_cut=False, work_limit=limit)
         if not r["truncated"] or r["seconds"] >= 0.6 * seconds:
             break
-        limit = int(limit * min(8.0, max(1.5, seconds / max(r["seconds"], 1e-3))))
+        limit = int(limit * min(4.0, max(1.5, 0.8 * seconds / max(r["seconds"], 1e-3))))
     return r, limit
 
 
@@ -397,7 +397,13 @@ def main():
     from paper_1507_01926_gb300 import mf
 
     g, csr = load_workload(args.grid3d)
-    opt = mf.default_options(device=torch.cuda.current_device())
+    # the autotuner's cached choice for this workload on this device (the packaged GB300 table when the
+    # user's cache has none), else the defaults
+    from paper_1507_01926_gb300 import autotune
+
+    hit = autotune.lookup(autotune.workload_key("grid3d", g.n, csr.m), autotune.device_name(torch.cuda.current_device()))
+    opt = hit[0] if hit else mf.default_options()
+    opt.device = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     row = torch.from_numpy(csr.row_offsets).to(dev)
     head = torch.from_numpy(csr.head).to(dev)
@@ -513,6 +519,10 @@ def main():
                      "model_bytes_per_launch": statistics.mean(mb)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
         "grid": [warm_stats["grid_blocks"], warm_stats["block_threads"]],
+        "options": {"tuned": "cached autotuner choice" if hit else "defaults (no cached choice)",
+                    **{f: getattr(opt, f) for f in ("gr_time_ratio", "gr_freq", "bin_thread", "bin_warp",
+                                                    "block_threads", "blocks_per_sm", "kernel_variant",
+                                                    "local_lists", "bfs_hops")}},
     }
     print(json.dumps(line), flush=True)
     G.close()

@@ -274,9 +274,10 @@ void mf_batch_destroy(mf_batch *b);
  * and keeps the fastest: coordinate descent over gr_time_ratio {0, 1, 2, 4},
  * gr_freq {0.25, 0.5, 1, 2}, bin_thread {2, 4, 8}, bin_warp {128, 1024, 8192},
  * the launch shape (threads per CTA, CTAs per SM) {(256, 2), (512, 1),
- * (128, 4), (256, 1)} and kernel_variant {0..3}, starting from g's current
- * options; candidates that are invalid together or do not fit the GPU are
- * skipped. A candidate's time is the median device time of spec->reps solves
+ * (128, 4), (256, 1)}, kernel_variant {0..3}, local_lists {0, 1} and
+ * bfs_hops {1, 4, 8, 16} (the last two only on graphs where they act),
+ * starting from g's current options; candidates that are invalid together or
+ * do not fit the GPU are skipped. A candidate's time is the median device time of spec->reps solves
  * (maximum flow value only, no per-arc outputs); spec->sweeps passes over the
  * coordinates at most (fewer when a pass changes nothing); no new candidate
  * starts once the solves took spec->time_budget_ms (0 = no limit). spec may

@@ -3,8 +3,9 @@
 //
 // The paper fixes its global-relabel constants (Algorithm 1: freq 0.5,
 // alpha 6, beta 12, taken from hi_pr) for a 40-core CPU. On the GPU the
-// relabel trigger, the degree bins of the discharge and BFS kernels and the
-// persistent kernel's launch shape trade off differently for each graph
+// relabel trigger, the degree bins of the discharge and BFS kernels, the
+// persistent kernel's launch shape, the CTA-local lists and the BFS levels per
+// grid barrier trade off differently for each graph
 // family (a 3D grid runs ~45,000 short rounds, a power-law graph a few
 // hundred wide ones), so they are measured: coordinate descent over a fixed
 // table of candidates, each candidate timed by the median device time of a
@@ -51,7 +52,7 @@ int measure(mf_graph *g, int reps, double *median_ms, std::vector<long long> *va
   return MF_OK;
 }
 
-enum Coord { GR_TIME_RATIO, GR_FREQ, BIN_THREAD, BIN_WARP, SHAPE, VARIANT, NCOORD };
+enum Coord { GR_TIME_RATIO, GR_FREQ, BIN_THREAD, BIN_WARP, SHAPE, VARIANT, LOCAL, HOPS, NCOORD };
 
 const double kTimeRatio[] = {0.0, 1.0, 2.0, 4.0};
 const double kFreq[] = {0.25, 0.5, 1.0, 2.0};
@@ -59,6 +60,8 @@ const int kBinThread[] = {2, 4, 8};
 const int kBinWarp[] = {128, 1024, 8192};
 const int kShape[][2] = {{256, 2}, {512, 1}, {128, 4}, {256, 1}};  // threads per CTA, CTAs per SM
 const int kVariant[] = {0, 1, 2, 3};
+const int kLocal[] = {0, 1};            // CTA-local lists off / on (K = block_threads / 2)
+const int kHops[] = {1, 4, 8, 16};      // BFS levels per grid barrier
 
 int candidates(Coord c) {
   switch (c) {
@@ -68,6 +71,8 @@ int candidates(Coord c) {
     case BIN_WARP: return 3;
     case SHAPE: return 4;
     case VARIANT: return 4;
+    case LOCAL: return 2;
+    case HOPS: return 4;
     default: return 0;
   }
 }
@@ -84,6 +89,8 @@ mf_options with(const mf_options &o, Coord c, int k) {
       x.blocks_per_sm = kShape[k][1];
       break;
     case VARIANT: x.kernel_variant = kVariant[k]; break;
+    case LOCAL: x.local_lists = kLocal[k]; break;
+    case HOPS: x.bfs_hops = kHops[k]; break;
     default: break;
   }
   return x;
@@ -132,6 +139,10 @@ int autotune(mf_graph *g, const mf_tune_spec *spec, mf_options *best, double *be
         if (budget > 0 && spent >= budget) goto done;
         const mf_options o = with(cur, (Coord)c, k);
         if (same(o, cur)) continue;
+        // the local lists and BFS hops act only on graphs whose vertices are all thread-sized
+        if ((c == LOCAL || c == HOPS) && keep_local_limit(o, g->max_degree, o.block_threads) == 0 &&
+            keep_local_limit(cur, g->max_degree, cur.block_threads) == 0)
+          continue;
         if (set_options(g, &o)) {  // an invalid combination or a shape that does not fit: skip it
           clear_error();
           continue;
