@@ -66,7 +66,8 @@ typedef struct mf_options {
   int32_t work_beta;
   /* Degree bins of the discharge and BFS kernels: a vertex of degree
    * <= bin_thread is handled by one thread, <= bin_warp by one warp, larger
-   * by a whole CTA. */
+   * by a whole CTA. bin_thread <= 8, or <= 16 with kernel_variant 4 (the
+   * BFS hands vertices of degree 9..16 to a warp either way). */
   int32_t bin_thread;
   int32_t bin_warp;
   /* Persistent-kernel shape: threads per CTA (multiple of 32, 64..512) and
@@ -91,7 +92,10 @@ typedef struct mf_options {
   double gr_time_ratio;
   /* Register budget of the persistent kernel: 0 = up to 128 registers per
    * thread, 1 = 85 (CTAs of <= 256 threads), 2 = 64 (<= 256 threads),
-   * 3 = 64 (<= 512 threads). Fewer registers keep more warps resident. */
+   * 3 = 64 (<= 512 threads), 4 = up to 255 (<= 256 threads, one CTA per SM)
+   * with a thread path for degrees up to 16 (bin_thread <= 16). Fewer
+   * registers keep more warps resident; variant 4 lets one thread discharge
+   * a vertex of degree 9..16 that would otherwise take a whole warp. */
   int32_t kernel_variant;
   /* 1: run the simple synchronous rounds of Section 3 instead of the improved
    * discharge of Section 3.1: each round pushes along admissible arcs with the
@@ -272,9 +276,10 @@ void mf_batch_destroy(mf_batch *b);
  * Autotuning (no counterpart in the paper, which fixes freq 0.5, alpha 6 and
  * beta 12 for a CPU). mf_autotune times solves of g under candidate options
  * and keeps the fastest: coordinate descent over gr_time_ratio {0, 1, 2, 4},
- * gr_freq {0.25, 0.5, 1, 2}, bin_thread {2, 4, 8}, bin_warp {128, 1024, 8192},
+ * gr_freq {0.25, 0.5, 1, 2}, bin_thread {2, 4, 8, 16}, bin_warp {128, 1024, 8192},
  * the launch shape (threads per CTA, CTAs per SM) {(256, 2), (512, 1),
- * (128, 4), (256, 1)}, kernel_variant {0..3}, local_lists {0, 1} and
+ * (128, 4), (256, 1)}, kernel_variant {0..4} (and variant 4 with
+ * bin_thread 16), local_lists {0, 1} and
  * bfs_hops {1, 4, 8, 16} (the last two only on graphs where they act),
  * starting from g's current options; candidates that are invalid together or
  * do not fit the GPU are skipped. A candidate's time is the median device time of spec->reps solves

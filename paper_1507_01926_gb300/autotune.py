@@ -13,7 +13,8 @@ Cache layout::
 A lookup that misses the user's cache falls back to ``tuned_gb300.json`` beside this module: the choices
 of the same search on a GB300 for the three standing workloads (the 256x256x128 3D grid, R-MAT scale 22 and
 the batch of 2048 layered graphs), written by ``python -m paper_1507_01926_gb300.autotune --out
-paper_1507_01926_gb300/tuned_gb300.json grid3d rmat layered``.
+paper_1507_01926_gb300/tuned_gb300.json <workload>`` (each entry's ``tuned_on`` field records the instances,
+reps and sweeps it was tuned with).
 """
 from __future__ import annotations
 
@@ -102,9 +103,10 @@ def tuned(target, key: str, path: str = DEFAULT_CACHE, reps: int = 3, sweeps: in
     return opts, ms, False
 
 
-def _standing_workload(name: str):
+def _standing_workload(name: str, batch_sample: int = 2048):
     """(key, target factory, note) of a standing workload: the 256x256x128 3D grid, R-MAT scale 22, or the
-    batch of 2048 layered graphs (tuned on its first 64 instances, stored under the full batch's key)."""
+    batch of 2048 layered graphs (tuned on its first `batch_sample` instances, stored under the full batch's
+    key)."""
     from . import inputs as I
 
     if name == "layered":
@@ -115,12 +117,13 @@ def _standing_workload(name: str):
             g = I.config3_instance(i, L, W)
             c = mf.build_csr(g.n, g.tail, g.head, g.cap)
             n_all, m_all = n_all + c.n, m_all + c.m
-            if i < 64:
+            if i < batch_sample:
                 c.arc_slot = None
                 csrs.append(c)
                 sts.append((g.s, g.t))
         key = workload_key("layered", n_all, m_all, len(params))
-        return key, (lambda: mf.Batch(csrs, sts)), "first 64 of the 2048 layered graphs, mf_batch_autotune"
+        which = "all" if len(csrs) == len(params) else f"first {len(csrs)} of the"
+        return key, (lambda: mf.Batch(csrs, sts)), f"{which} 2048 layered graphs, mf_batch_autotune"
     g = {"grid3d": I.config1, "rmat": I.config2}[name]()
     c = mf.build_csr(g.n, g.tail, g.head, g.cap)
     return workload_key(name, g.n, c.m), (lambda: mf.Graph.from_csr(c, g.s, g.t)), f"{g.name}, mf_autotune"
@@ -135,10 +138,11 @@ def main(argv=None) -> int:
     ap.add_argument("--out", default=DEFAULT_CACHE)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--batch-sample", type=int, default=2048, help="layered instances the batch is tuned on")
     a = ap.parse_args(argv)
     dev = device_name(0)
     for name in a.workloads:
-        key, make, note = _standing_workload(name)
+        key, make, note = _standing_workload(name, a.batch_sample)
         with make() as target:
             opts, ms = target.autotune(reps=a.reps, sweeps=a.sweeps)
         store(key, dev, opts, ms, a.out)

@@ -238,7 +238,7 @@ int launch_config(mf_graph *g) {
 int check_options(const mf_options *o) {
   if (o->block_threads < 64 || o->block_threads > 512 || o->block_threads % 32)
     return fail(MF_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [64, 512]");
-  if (o->bin_thread < 0 || o->bin_thread > 8) return fail(MF_ERR_INVALID_ARG, "bin_thread must be in [0, 8]");
+  if (o->bin_thread < 0 || o->bin_thread > 16) return fail(MF_ERR_INVALID_ARG, "bin_thread must be in [0, 16]");
   if (o->bin_warp < o->bin_thread) return fail(MF_ERR_INVALID_ARG, "bin_warp must be >= bin_thread");
   if (!(o->gr_freq > 0)) return fail(MF_ERR_INVALID_ARG, "gr_freq must be > 0");
   if (o->gr_alpha < 0 || o->work_beta < 0) return fail(MF_ERR_INVALID_ARG, "gr_alpha, work_beta must be >= 0");
@@ -254,6 +254,9 @@ int check_options(const mf_options *o) {
   if (o->block_threads > solver_variant_max_threads(o->kernel_variant))
     return fail(MF_ERR_INVALID_ARG, "kernel_variant %d takes at most %d threads per CTA", o->kernel_variant,
                 solver_variant_max_threads(o->kernel_variant));
+  if (o->bin_thread > solver_variant_max_bin_thread(o->kernel_variant))
+    return fail(MF_ERR_INVALID_ARG, "kernel_variant %d takes bin_thread <= %d", o->kernel_variant,
+                solver_variant_max_bin_thread(o->kernel_variant));
   return MF_OK;
 }
 

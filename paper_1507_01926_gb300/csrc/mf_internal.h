@@ -54,6 +54,7 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
 int keep_local_limit(const mf_options &o, long long max_degree, int block_threads);
 int solver_variants();
 int solver_variant_max_threads(int variant);
+int solver_variant_max_bin_thread(int variant);
 int solver_occupancy(int block_threads, int *blocks_per_sm, int variant);
 cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant);
 int set_options(mf_graph *g, const mf_options *o);

@@ -522,14 +522,15 @@ __device__ __forceinline__ void retire_dead(const Dev &D, const RoundCtx &R, int
   if (ad) *exc_ptr(D, v) = __ldcg(exc_ptr(D, v)) + ad;
 }
 
-// One thread, deg <= KT: arcs cached in registers for all passes. With
+// One thread, deg <= KTD: arcs cached in registers for all passes. With
 // `pre`, the heads were loaded during the last grid barrier (prefetch_next)
 // and dv is not known yet: the vertex record, the residuals and all
 // neighbours' label slots are read in one round trip, then a vertex whose
 // label reached the cap is retired.
+template <int KTD>
 __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const RoundCtx &R, int v, int beg,
                                                  int deg, int dv, int cap_v, TStat &st, long long &work, bool pre) {
-  int wv[KT], rs[KT], dw[KT], rv[KT];
+  int wv[KTD], rs[KTD], dw[KTD], rv[KTD];
   unsigned act = 0;
   // excess: own value plus what neighbours delivered so far; exactly that
   // delivered amount is taken out of addedExcess at the end (later deliveries stay)
@@ -539,8 +540,8 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
     const int2 own = load_slot(D, R.p, v);
     ea = load_ea(D, v);
 #pragma unroll
-    for (int i = 0; i < KT; i++) {
-      wv[i] = i < deg ? sh.phead[i][threadIdx.x] : 0;
+    for (int i = 0; i < KTD; i++) {
+      wv[i] = (i < KT && i < deg) ? sh.phead[i < KT ? i : 0][threadIdx.x] : 0;
       rs[i] = 0;
       dw[i] = 0;
       rv[i] = 0;
@@ -559,12 +560,12 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
     }
     st.visits_dis++;
 #pragma unroll
-    for (int i = 0; i < KT; i++)
+    for (int i = 0; i < KTD; i++)
       if (rs[i] <= 0) act &= ~(1u << i);
   } else {
     ea = load_ea(D, v);
 #pragma unroll
-    for (int i = 0; i < KT; i++) {
+    for (int i = 0; i < KTD; i++) {
       wv[i] = 0;
       rs[i] = 0;
       dw[i] = 0;
@@ -576,7 +577,7 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
       }
     }
 #pragma unroll
-    for (int i = 0; i < KT; i++)
+    for (int i = 0; i < KTD; i++)
       if (rs[i] > 0) {
         const int2 x = load_slot(D, R.p, wv[i]);
         dw[i] = x.x;
@@ -591,14 +592,14 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
   // Discovery test-and-set results are collected per arc and read only after
   // the discharge, so the atomics of several pushes are in flight together.
   unsigned tested = 0;
-  int prev_stamp[KT];
+  int prev_stamp[KTD];
 #pragma unroll
-  for (int i = 0; i < KT; i++) prev_stamp[i] = R.r + 1;
+  for (int i = 0; i < KTD; i++) prev_stamp[i] = R.r + 1;
   for (;;) {
     int newl = cap_v;
     bool skipped = false;
 #pragma unroll
-    for (int i = 0; i < KT; i++) {
+    for (int i = 0; i < KTD; i++) {
       if (i < deg && ex > 0 && rs[i] > 0) {
         st.scans_dis++;
         const bool adm = (dp == dw[i] + 1);
@@ -638,7 +639,7 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
   else
     finish_vertex(D, sh, R, v, dp, ex, cap_v);
 #pragma unroll
-  for (int i = 0; i < KT; i++)
+  for (int i = 0; i < KTD; i++)
     if (prev_stamp[i] != R.r + 1) qpush(D, sh, R.next, wv[i]);
   flush_sink(D, sink, to_sink);
 }
@@ -819,6 +820,7 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
 // the merge step of the previous round (label carried into the next slot,
 // addedExcess folded into the excess). Both kinds run side by side on
 // different threads. Discoveries go to generation gen + 1.
+template <int KTD>
 __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, long long rnd, TStat &st,
                             unsigned long long &t_phase0) {
   const RoundCtx R{r, r & 1, gen + 1};
@@ -892,7 +894,7 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       if (lane == leader) cls = 0;
       discharge_warp(D, sh, R, pv, pdv, pcap, st, work);
     }
-    if (cls == 1 || cls == 4) discharge_thread(D, sh, R, v, beg, deg, dv, cap_v, st, work, cls == 4);
+    if (cls == 1 || cls == 4) discharge_thread<KTD>(D, sh, R, v, beg, deg, dv, cap_v, st, work, cls == 4);
     __syncwarp();
   }
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1043,47 +1045,49 @@ __device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int l, 
   if (cf > 0 && bfs_offer(D, w, l)) qpush(D, sh, next, w);
 }
 
-// One thread, deg <= KT, loads issued together (with `pre`, the heads were
-// loaded during the last grid barrier).
+// One thread, deg <= KTD, loads issued together (with `pre`, deg <= KT and the
+// heads were loaded during the last grid barrier).
+template <int KTD>
 __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, int deg, int l, bool reverse, int next,
                                            bool pre) {
-  int w[KT], cf[KT];
-  bool got[KT];
+  int w[KTD], cf[KTD];
+  bool got[KTD];
 #pragma unroll
-  for (int i = 0; i < KT; i++) {
+  for (int i = 0; i < KTD; i++) {
     w[i] = 0;
     cf[i] = 0;
     if (i < deg) {
-      w[i] = pre ? sh.phead[i][threadIdx.x] : __ldg(&D.head[beg + i]);
+      w[i] = (pre && i < KT) ? sh.phead[i < KT ? i : 0][threadIdx.x] : __ldg(&D.head[beg + i]);
       const int2 x = __ldcg(&D.rr[beg + i]);
       cf[i] = reverse ? x.y : x.x;
     }
   }
   if (D.bfs_hops > 1) {
     // all offers and the offered vertices' row offsets in flight together
-    int rb[KT], re[KT];
+    int rb[KTD], re[KTD];
 #pragma unroll
-    for (int i = 0; i < KT; i++) {
+    for (int i = 0; i < KTD; i++) {
       got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
       rb[i] = cf[i] > 0 ? __ldg(&D.row[w[i]]) : 0;
       re[i] = cf[i] > 0 ? __ldg(&D.row[w[i] + 1]) : 0;
     }
 #pragma unroll
-    for (int i = 0; i < KT; i++)
+    for (int i = 0; i < KTD; i++)
       if (got[i]) qpush_row(D, sh, next, w[i], rb[i], re[i] - rb[i]);
     return;
   }
   // all offers first (in flight together), then the appends
 #pragma unroll
-  for (int i = 0; i < KT; i++) got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
+  for (int i = 0; i < KTD; i++) got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
 #pragma unroll
-  for (int i = 0; i < KT; i++)
+  for (int i = 0; i < KTD; i++)
     if (got[i]) qpush(D, sh, next, w[i]);
 }
 
 // One BFS level: expands the list of generation gen into generation gen + 1,
 // then (D.bfs_hops > 1) up to bfs_hops - 1 more levels of the vertices this
 // CTA reached itself, while they fit one per thread.
+template <int KTD>
 __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat &st) {
   const int next = gen + 1;
   const Sweep sw = make_sweep(sh.lq[gen % 3], sh.lqn[gen % 3], nullptr, 0, list_of(D, gen), list_count(D, sh, gen),
@@ -1107,7 +1111,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
         beg = __ldg(&D.row[v]);
         deg = __ldg(&D.row[v + 1]) - beg;
       }
-      cls = deg <= KT ? 1 : (deg <= D.bin_warp ? 2 : 3);
+      cls = deg <= KTD ? 1 : (deg <= D.bin_warp ? 2 : 3);
       st.scans_bfs += deg;
       st.visits_bfs++;
     }
@@ -1140,7 +1144,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
       for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, pl, reverse, next);
       __syncwarp();
     }
-    if (cls == 1) bfs_thread(D, sh, beg, deg, l, reverse, next, pre);
+    if (cls == 1) bfs_thread<KTD>(D, sh, beg, deg, l, reverse, next, pre);
     __syncwarp();
   }
   // more levels inside the CTA (only on graphs whose vertices are all
@@ -1166,7 +1170,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
         const int l = bfs_take(D, v) + 1;
         st.scans_bfs += deg;
         st.visits_bfs++;
-        bfs_thread(D, sh, beg, deg, l, reverse, next, false);
+        bfs_thread<KT>(D, sh, beg, deg, l, reverse, next, false);
       }
     }
   }
@@ -1177,6 +1181,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
 // `excess_seeds`, every vertex holding excess whose label lies in [1, cap] is
 // a seed as well (cut from the maximum preflow). Returns false on error. On
 // return the last list generation (gen) is empty and no vertex is queued.
+template <int KTD>
 __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *blockers, int nterm, bool reverse,
                     bool excess_seeds, int &gen, TStat &st, int where) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -1217,7 +1222,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
       if (k < D.trace_lv_cap) D.trace_lv[k] = (int)fcount;
     }
     const unsigned long long t0 = timer ? gtimer() : 0;
-    bfs_level(D, sh, gen, reverse, st);
+    bfs_level<KTD>(D, sh, gen, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
     if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
     gen++;
@@ -1243,9 +1248,10 @@ __device__ __forceinline__ int bfs_label(unsigned long long x, int cap) {
 // cap n, sources n + 1, both label slots get the result, addedExcess is folded
 // into the excess, and every vertex with excess and 0 < d < n is stamped
 // active. Result: list generation gen.
+template <int KTD>
 __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const int *sources, int r, int &gen,
                                TStat &st) {
-  if (!bfs(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2)) return false;
+  if (!bfs<KTD>(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2)) return false;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   const int next = gen + 1;
   const int p = r & 1;
@@ -1296,6 +1302,7 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
 
 // Rounds of Algorithm 1 toward `sinks` until no vertex is active right after a
 // global relabel (or, in MODE_ROUNDS, until stop_rounds rounds ran).
+template <int KTD>
 __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int *sources, int &r, int &gen,
                           long long &rnd, bool phase1, TStat &st) {
   long long since_gr = LLONG_MAX;
@@ -1307,7 +1314,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     if (since_gr > D.gr_threshold || time_req) {
       r++;  // fresh stamp: marks of the discarded working set are stale
       const unsigned long long t0 = timer ? gtimer() : 0;
-      if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st)) return false;
       if (timer) {
         last_gr_end = gtimer();
         last_gr_ns = last_gr_end - t0;
@@ -1339,7 +1346,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     }
     fresh = false;
     unsigned long long tp = t0;
-    round_phase(D, sh, r, gen, prev_valid, rnd, st, tp);
+    round_phase<KTD>(D, sh, r, gen, prev_valid, rnd, st, tp);
     if (!grid_sync(D, sh, 4, D.simple ? PF_NONE : PF_ROUND, gen + 1, gen)) return false;
     if (D.simple) {
       relabel_phase(D, sh, r, gen, rnd, st);
@@ -1366,7 +1373,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     if (timer) D.ctl->stopped_round = (int)rounds;
     if (D.final_gr) {
       r++;
-      if (!global_relabel(D, sh, sinks, sources, r, gen, st)) return false;
+      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st)) return false;
     } else if (!fresh) {
       if (!settle(D, sh, r & 1)) return false;
     }
@@ -1376,6 +1383,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
 
 // ------------------------------------------------------------------ kernel
 
+template <int KTD>
 __device__ __forceinline__ void solve_body(const Dev &D) {
   __shared__ Shared sh;
   if (threadIdx.x == 0) {
@@ -1418,7 +1426,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   }
   int r = 0, gen = 0;
   long long rnd = 0;
-  if (ok) ok = run_phase(D, sh, D.snk, D.src, r, gen, rnd, true, st);
+  if (ok) ok = run_phase<KTD>(D, sh, D.snk, D.src, r, gen, rnd, true, st);
   if (ok && D.mode == MODE_SOLVE) {
     if (tid == 0) D.ctl->t_preflow = gtimer();
     for (int k = tid; k < D.ninst; k += nthr) {
@@ -1428,10 +1436,10 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
     }
     if (D.cut_only) {
       // S_min from the maximum preflow: reachable from s and every excess vertex.
-      ok = bfs(D, sh, D.src, nullptr, D.ninst, false, true, gen, st, 6);
+      ok = bfs<KTD>(D, sh, D.src, nullptr, D.ninst, false, true, gen, st, 6);
     } else {
       // Phase 2: return the excess that cannot reach t to s (s plays the sink).
-      ok = run_phase(D, sh, D.src, D.snk, r, gen, rnd, false, st);
+      ok = run_phase<KTD>(D, sh, D.src, D.snk, r, gen, rnd, false, st);
       if (ok) {
         long long left = 0;
         for (int v = tid; v < D.n; v += nthr) {
@@ -1447,7 +1455,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
         }
       }
       // Cut: BFS from s over arcs with positive residual.
-      if (ok) ok = bfs(D, sh, D.src, nullptr, D.ninst, false, false, gen, st, 9);
+      if (ok) ok = bfs<KTD>(D, sh, D.src, nullptr, D.ninst, false, false, gen, st, 9);
     }
     if (ok) {
       if (D.out_cut) {
@@ -1487,9 +1495,11 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
 
 // Register-budget variants of the same kernel: __launch_bounds__(MAXT, MINB)
 // caps registers at 65536 / (MAXT * MINB) so that more warps stay resident.
-template <int MAXT, int MINB>
+// KTD is the largest degree a single thread discharges (arcs cached in
+// registers); 16 needs the register budget of one 256-thread CTA per SM.
+template <int MAXT, int MINB, int KTD>
 __global__ void __launch_bounds__(MAXT, MINB) solve_kernel(Dev D) {
-  solve_body(D);
+  solve_body<KTD>(D);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1497,13 +1507,15 @@ __global__ void __launch_bounds__(MAXT, MINB) solve_kernel(Dev D) {
 struct Variant {
   const void *fn;
   int max_threads;
+  int max_bin_thread;  // KTD
 };
 
 static const Variant kVariants[] = {
-    {(const void *)solve_kernel<512, 1>, 512},  // up to 128 registers
-    {(const void *)solve_kernel<256, 3>, 256},  // up to 85
-    {(const void *)solve_kernel<256, 4>, 256},  // up to 64
-    {(const void *)solve_kernel<512, 2>, 512},  // up to 64
+    {(const void *)solve_kernel<512, 1, KT>, 512, KT},  // up to 128 registers
+    {(const void *)solve_kernel<256, 3, KT>, 256, KT},  // up to 85
+    {(const void *)solve_kernel<256, 4, KT>, 256, KT},  // up to 64
+    {(const void *)solve_kernel<512, 2, KT>, 512, KT},  // up to 64
+    {(const void *)solve_kernel<256, 1, 16>, 256, 16},  // up to 255; one thread discharges up to 16 slots
 };
 constexpr int NUM_VARIANTS = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1511,6 +1523,10 @@ int solver_variants() { return NUM_VARIANTS; }
 
 int solver_variant_max_threads(int variant) {
   return variant >= 0 && variant < NUM_VARIANTS ? kVariants[variant].max_threads : 0;
+}
+
+int solver_variant_max_bin_thread(int variant) {
+  return variant >= 0 && variant < NUM_VARIANTS ? kVariants[variant].max_bin_thread : 0;
 }
 
 int keep_local_limit(const mf_options &o, long long max_degree, int block_threads) {

@@ -56,10 +56,13 @@ enum Coord { GR_TIME_RATIO, GR_FREQ, BIN_THREAD, BIN_WARP, SHAPE, VARIANT, LOCAL
 
 const double kTimeRatio[] = {0.0, 1.0, 2.0, 4.0};
 const double kFreq[] = {0.25, 0.5, 1.0, 2.0};
-const int kBinThread[] = {2, 4, 8};
+const int kBinThread[] = {2, 4, 8, 16};
 const int kBinWarp[] = {128, 1024, 8192};
 const int kShape[][2] = {{256, 2}, {512, 1}, {128, 4}, {256, 1}};  // threads per CTA, CTAs per SM
-const int kVariant[] = {0, 1, 2, 3};
+// kernel_variant, with the bin_thread it is tried with (-1: unchanged); variant
+// 4's 16-slot thread path is tried together with bin_thread 16, which no other
+// variant accepts (one coordinate at a time could not reach the pair)
+const int kVariant[][2] = {{0, -1}, {1, -1}, {2, -1}, {3, -1}, {4, -1}, {4, 16}};
 const int kLocal[] = {0, 1};            // CTA-local lists off / on (K = block_threads / 2)
 const int kHops[] = {1, 4, 8, 16};      // BFS levels per grid barrier
 
@@ -67,10 +70,10 @@ int candidates(Coord c) {
   switch (c) {
     case GR_TIME_RATIO: return 4;
     case GR_FREQ: return 4;
-    case BIN_THREAD: return 3;
+    case BIN_THREAD: return 4;
     case BIN_WARP: return 3;
     case SHAPE: return 4;
-    case VARIANT: return 4;
+    case VARIANT: return 6;
     case LOCAL: return 2;
     case HOPS: return 4;
     default: return 0;
@@ -88,7 +91,10 @@ mf_options with(const mf_options &o, Coord c, int k) {
       x.block_threads = kShape[k][0];
       x.blocks_per_sm = kShape[k][1];
       break;
-    case VARIANT: x.kernel_variant = kVariant[k]; break;
+    case VARIANT:
+      x.kernel_variant = kVariant[k][0];
+      if (kVariant[k][1] >= 0) x.bin_thread = kVariant[k][1];
+      break;
     case LOCAL: x.local_lists = kLocal[k]; break;
     case HOPS: x.bfs_hops = kHops[k]; break;
     default: break;

@@ -84,11 +84,14 @@ def test_degree_bins_agree(gpu, bins):
         solve_and_compare(gpu, g, opt)
 
 
-@pytest.mark.parametrize("variant,bt", [(0, 256), (1, 256), (2, 256), (3, 512), (2, 128)])
-def test_kernel_variants_agree(gpu, variant, bt):
-    """Every register-budget variant of the persistent kernel gives the same unique results."""
-    opt = gpu.default_options(kernel_variant=variant, block_threads=bt)
-    for g in (I.grid3d(18, 20, 10, seed=variant), I.rmat(11, 8, 40 + variant), I.grid2d(40, 60, variant)):
+@pytest.mark.parametrize("variant,bt,bin_thread", [(0, 256, 8), (1, 256, 8), (2, 256, 8), (3, 512, 8), (2, 128, 8),
+                                                   (4, 256, 8), (4, 256, 16), (4, 128, 12)])
+def test_kernel_variants_agree(gpu, variant, bt, bin_thread):
+    """Every register-budget variant of the persistent kernel gives the same unique results (variant 4 also
+    with the 16-slot thread path, which the layered graphs' degree-9..16 vertices take)."""
+    opt = gpu.default_options(kernel_variant=variant, block_threads=bt, bin_thread=bin_thread)
+    for g in (I.grid3d(18, 20, 10, seed=variant), I.rmat(11, 8, 40 + variant), I.grid2d(40, 60, variant),
+              I.layered(12, 90, 50 + variant), I.random_graph(60, 700, 60 + variant, cap=(1, 40))):
         solve_and_compare(gpu, g, opt)
 
 
