@@ -48,6 +48,16 @@ def model_bytes(st: dict, n: int, m: int) -> int:
                + B_VERTEX_FIXED * n + B_VERTEX_GR * n * st["global_relabels"])
 
 
+def apply_overrides(opt, args):
+    """Sets the mf_options fields given by --options (a JSON object) on opt."""
+    if args.options:
+        for k, v in json.loads(args.options).items():
+            if not hasattr(opt, k):
+                raise KeyError(k)
+            setattr(opt, k, v)
+    return opt
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -248,6 +258,7 @@ def run_batch(args):
     opt = hit[0] if hit else mf.default_options()
     opt.device = 0
     opt.use_graph = 0 if args.no_graph else 1
+    apply_overrides(opt, args)
     popt = mf.default_options(device=0, use_graph=opt.use_graph)
     # plain: one launch per instance, graphs already resident
     k = min(args.plain_count, len(csrs))
@@ -302,7 +313,8 @@ def run_batch(args):
                          "frac": mb / st["solve_ms"] * 1e-6 / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "mf::solve_kernel", "model_bytes_per_launch": mb,
                          "scans_per_launch": st["scans_discharge"] + st["scans_bfs"]},
-            "options": {"tuned": "cached autotuner choice" if hit else "defaults (no cached choice)",
+            "options": {"tuned": ("cached autotuner choice" if hit else "defaults (no cached choice)")
+                        + (f", overridden by {args.options}" if args.options else ""),
                         "use_graph": int(opt.use_graph),
                         **{f: getattr(opt, f) for f in ("gr_time_ratio", "gr_freq", "bin_thread", "bin_warp",
                                                         "block_threads", "blocks_per_sm", "kernel_variant")}}}
@@ -379,6 +391,7 @@ def main():
     ap.add_argument("--plain-count", type=int, default=128)
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--no-graph", action="store_true", help="batch workload: launch directly, no CUDA graphs")
+    ap.add_argument("--options", default="", help="JSON object of mf_options fields applied over the chosen options")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -415,6 +428,7 @@ def main():
     hit = autotune.lookup(autotune.workload_key("grid3d", g.n, csr.m), autotune.device_name(torch.cuda.current_device()))
     opt = hit[0] if hit else mf.default_options()
     opt.device = torch.cuda.current_device()
+    apply_overrides(opt, args)
     stream = torch.cuda.Stream()
     row = torch.from_numpy(csr.row_offsets).to(dev)
     head = torch.from_numpy(csr.head).to(dev)
@@ -530,7 +544,8 @@ def main():
                      "model_bytes_per_launch": statistics.mean(mb)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
         "grid": [warm_stats["grid_blocks"], warm_stats["block_threads"]],
-        "options": {"tuned": "cached autotuner choice" if hit else "defaults (no cached choice)",
+        "options": {"tuned": ("cached autotuner choice" if hit else "defaults (no cached choice)")
+                        + (f", overridden by {args.options}" if args.options else ""),
                     **{f: getattr(opt, f) for f in ("gr_time_ratio", "gr_freq", "bin_thread", "bin_warp",
                                                     "block_threads", "blocks_per_sm", "kernel_variant",
                                                     "local_lists", "bfs_hops")}},
