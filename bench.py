@@ -124,7 +124,7 @@ def load_workload(shape=None):
     from paper_1507_01926_gb300 import inputs, mf
 
     if shape is None or tuple(shape) == (256, 256, 128):
-        g = inputs.config1()
+        g = inputs.grid3d_256x256x128()
     else:
         g = inputs.grid3d(*shape, seed=inputs.BASE_SEED + 1)
     csr = mf.build_csr(g.n, g.tail, g.head, g.cap)
@@ -141,7 +141,7 @@ def kernel_source_hash() -> str:
 
 
 def golden_value():
-    p = os.path.join(ROOT, "tests", "golden", "config1.json")
+    p = os.path.join(ROOT, "tests", "golden", "grid3d_256x256x128.json")
     if os.path.exists(p):
         return json.load(open(p))["value"]
     return None
@@ -203,7 +203,7 @@ def run_reference(args):
 
     import oracle
 
-    g = inputs.config1()
+    g = inputs.grid3d_256x256x128()
     per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
     _, limit = sized_oracle_run(g, per_step)
     for _ in range(args.warmup):
@@ -237,11 +237,11 @@ def run_batch(args):
     from paper_1507_01926_gb300 import inputs, mf
 
     torch.cuda.set_device(0)
-    params = inputs.config3_params(args.batch_count)
+    params = inputs.layered_batch_params(args.batch_count)
     t0 = time.perf_counter()
     csrs, sts, ns_list = [], [], []
     for i, (L, W) in enumerate(params):  # build one at a time: only the CSRs stay in host memory
-        g = inputs.config3_instance(i, L, W)
+        g = inputs.layered_batch_instance(i, L, W)
         c = mf.build_csr(g.n, g.tail, g.head, g.cap)
         c.arc_slot = None
         csrs.append(c)
@@ -331,11 +331,11 @@ def run_serve(args):
     from paper_1507_01926_gb300 import inputs, mf
 
     torch.cuda.set_device(0)
-    reqs = inputs.config4_requests(args.requests, rate_per_s=1.0)
+    reqs = inputs.serving_stream_requests(args.requests, rate_per_s=1.0)
     t0 = time.perf_counter()
     items = []
     for i, (_, kind, size) in enumerate(reqs):
-        g = inputs.config4_instance(i, kind, size)
+        g = inputs.serving_stream_instance(i, kind, size)
         items.append((g, mf.build_csr(g.n, g.tail, g.head, g.cap)))
     prep_s = time.perf_counter() - t0
     budget = 64 << 30

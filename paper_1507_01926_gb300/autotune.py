@@ -110,11 +110,11 @@ def _standing_workload(name: str, batch_sample: int = 2048):
     from . import inputs as I
 
     if name == "layered":
-        params = I.config3_params()
+        params = I.layered_batch_params()
         n_all = m_all = 0
         csrs, sts = [], []
         for i, (L, W) in enumerate(params):
-            g = I.config3_instance(i, L, W)
+            g = I.layered_batch_instance(i, L, W)
             c = mf.build_csr(g.n, g.tail, g.head, g.cap)
             n_all, m_all = n_all + c.n, m_all + c.m
             if i < batch_sample:
@@ -124,7 +124,7 @@ def _standing_workload(name: str, batch_sample: int = 2048):
         key = workload_key("layered", n_all, m_all, len(params))
         which = "all" if len(csrs) == len(params) else f"first {len(csrs)} of the"
         return key, (lambda: mf.Batch(csrs, sts)), f"{which} 2048 layered graphs, mf_batch_autotune"
-    g = {"grid3d": I.config1, "rmat": I.config2}[name]()
+    g = {"grid3d": I.grid3d_256x256x128, "rmat": I.rmat_s22_ef16}[name]()
     c = mf.build_csr(g.n, g.tail, g.head, g.cap)
     return workload_key(name, g.n, c.m), (lambda: mf.Graph.from_csr(c, g.s, g.t)), f"{g.name}, mf_autotune"
 

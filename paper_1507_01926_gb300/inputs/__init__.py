@@ -3,19 +3,21 @@
 This module holds only structure and random numbers (see ``gen.c``): vertex numbering, arc lists and
 capacities of the workload families. It contains none of the max-flow arithmetic.
 
-Workload recipes (seed = 150701926 + config index; instance i of a batch uses seed * 2**20 + i):
+Workload recipes (seed = 150701926 + k with k = 0..4 in the order below; instance i of a batch or stream
+uses seed * 2**20 + i):
 
-* ``config0``: 64x64 4-connected grid, neighbour capacity U[1,100] per direction, every pixel gets s->p
+* ``grid2d_64x64``: 64x64 4-connected grid, neighbour capacity U[1,100] per direction, every pixel gets s->p
   (probability 1/2) or p->t with capacity U[1,1000].
-* ``config1``: 256x256x128 6-connected grid, capacity U[1,1000] per direction, s -> face z=0 and
+* ``grid3d_256x256x128``: 256x256x128 6-connected grid, capacity U[1,1000] per direction, s -> face z=0 and
   face z=127 -> t at 10^6.
-* ``config2``: R-MAT scale 22, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05), self-loops and
+* ``rmat_s22_ef16``: R-MAT scale 22, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05), self-loops and
   duplicates dropped, capacity U[1,1000]; s = max out-degree, t = max in-degree among the rest.
-* ``config3``: 2048 layered graphs, L ~ logU[16,256], W ~ logU[64,4096], 4 next-layer arcs + 1
+* ``layered_batch_params`` / ``layered_batch_instance``: 2048 layered graphs, L ~ logU[16,256], W ~ logU[64,4096], 4 next-layer arcs + 1
   in-layer arc per vertex, capacity U[1,10000], terminals at 10^6.
-* ``config4``: a stream of requests, half 2D grids (side ~ logU[32,1024], config0 rule), half
+* ``serving_stream_requests`` / ``serving_stream_instance``: a stream of requests, half 2D grids
+  (side ~ logU[32,1024], terminals as in grid2d_64x64), half
   multi-frame grids (F ~ U[4,64] frames of 128x128, in-frame U[1,1000], frame-to-frame permutation
-  arcs U[1,100], config0 terminal rule), Poisson arrivals.
+  arcs U[1,100], terminals as in grid2d_64x64), Poisson arrivals.
 """
 from __future__ import annotations
 
@@ -157,43 +159,43 @@ def draw_u01(seed, stream, i) -> float:
     return float(_L().mfg_u01(seed, stream, i))
 
 
-# ---------------------------------------------------------------- workload configs
+# ---------------------------------------------------------------- standing workloads
 
-def config0() -> Instance:
+def grid2d_64x64() -> Instance:
     """64x64 2D grid (4,098 vertices)."""
     g = grid2d(64, 64, BASE_SEED + 0)
     g.name = "grid2d_64x64"
     return g
 
 
-def config1() -> Instance:
+def grid3d_256x256x128() -> Instance:
     """256x256x128 3D grid (8,388,610 vertices)."""
     g = grid3d(256, 256, 128, BASE_SEED + 1)
     g.name = "grid3d_256x256x128"
     return g
 
 
-def config2() -> Instance:
+def rmat_s22_ef16() -> Instance:
     """R-MAT scale 22, edge factor 16."""
     g = rmat(22, 16, BASE_SEED + 2)
     g.name = "rmat_s22_ef16"
     return g
 
 
-def config3_params(count: int = 2048):
+def layered_batch_params(count: int = 2048):
     """(L, W) of each layered instance of the batch, from the batch seed."""
     seed = BASE_SEED + 3
     return [(draw_logunif(seed, 1, 2 * i, 16, 256), draw_logunif(seed, 1, 2 * i + 1, 64, 4096))
             for i in range(count)]
 
 
-def config3_instance(i: int, L: int, W: int) -> Instance:
+def layered_batch_instance(i: int, L: int, W: int) -> Instance:
     g = layered(L, W, (BASE_SEED + 3) * (1 << 20) + i)
     g.name = f"layered_{i}_{L}x{W}"
     return g
 
 
-def config4_requests(count: int = 20000, rate_per_s: float = 1.0):
+def serving_stream_requests(count: int = 20000, rate_per_s: float = 1.0):
     """Request descriptors of the serving stream: (arrival_s, kind, size) with kind 'grid' (size = side)
     or 'frames' (size = F). Inter-arrival times are exponential with the given rate."""
     seed = BASE_SEED + 4
@@ -209,7 +211,7 @@ def config4_requests(count: int = 20000, rate_per_s: float = 1.0):
     return out
 
 
-def config4_instance(i: int, kind: str, size: int) -> Instance:
+def serving_stream_instance(i: int, kind: str, size: int) -> Instance:
     seed = (BASE_SEED + 4) * (1 << 20) + i
     if kind == "grid":
         return grid2d(size, size, seed)

@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libmf.so")
-    config.addinivalue_line("markers", "slow: large workload (full-size configs)")
+    config.addinivalue_line("markers", "slow: large workload (full-size instances)")
 
 
 @pytest.fixture(scope="session")

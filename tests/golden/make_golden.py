@@ -1,6 +1,6 @@
 """Writes the stored expected results of the large workloads by running the CPU oracle.
 
-Usage: python tests/golden/make_golden.py [config1] [config2] ...
+Usage: python tests/golden/make_golden.py [grid3d_256x256x128] [rmat_s22_ef16] ...
 
 Only the oracle and the seeded input generators are called; nothing comes from the GPU path. For each
 workload the file ``tests/golden/<name>.json`` records the instance shape (n, m, s, t), the maximum
@@ -23,9 +23,9 @@ import oracle  # noqa: E402
 from paper_1507_01926_gb300 import inputs  # noqa: E402
 
 WORKLOADS = {
-    "config0": inputs.config0,
-    "config1": inputs.config1,
-    "config2": inputs.config2,
+    "grid2d_64x64": inputs.grid2d_64x64,
+    "grid3d_256x256x128": inputs.grid3d_256x256x128,
+    "rmat_s22_ef16": inputs.rmat_s22_ef16,
 }
 
 

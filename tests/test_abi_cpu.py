@@ -91,7 +91,7 @@ def test_build_csr_pairs_antiparallel_arcs(built):
 def test_build_csr_grid_slot_count(built):
     from paper_1507_01926_gb300 import mf
 
-    g = I.config0()
+    g = I.grid2d_64x64()
     c = mf.build_csr(g.n, g.tail, g.head, g.cap)
     assert c.m == 24320
     check_csr(c, g.tail, g.head, g.cap)

@@ -23,7 +23,7 @@ def digest(cut):
     return hashlib.sha256(np.packbits(cut.astype(np.uint8), bitorder="little").tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["config0", "config1", "config2"])
+@pytest.mark.parametrize("name", ["grid2d_64x64", "grid3d_256x256x128", "rmat_s22_ef16"])
 def test_full_size_against_golden(gpu, name):
     gold = json.load(open(os.path.join(GOLD, f"{name}.json")))
     g = getattr(I, name)()
@@ -36,9 +36,9 @@ def test_full_size_against_golden(gpu, name):
     assert not bad, bad
 
 
-def test_config1_cut_only_and_repeat(gpu):
-    gold = json.load(open(os.path.join(GOLD, "config1.json")))
-    g = I.config1()
+def test_grid3d_256x256x128_cut_only_and_repeat(gpu):
+    gold = json.load(open(os.path.join(GOLD, "grid3d_256x256x128.json")))
+    g = I.grid3d_256x256x128()
     csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
     with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(cut_only=1)) as G:
         for _ in range(2):

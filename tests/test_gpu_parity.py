@@ -41,13 +41,13 @@ def test_random_dense_hubs(gpu, seed):
     solve_and_compare(gpu, g)
 
 
-def test_config0(gpu):
+def test_grid2d_64x64(gpu):
     import json
     import os
 
-    g = I.config0()
+    g = I.grid2d_64x64()
     value, stats = solve_and_compare(gpu, g)
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config0.json")))
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid2d_64x64.json")))
     assert value == gold["value"]
     assert stats["rounds"] > 0 and stats["global_relabels"] >= 2
 

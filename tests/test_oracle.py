@@ -209,8 +209,8 @@ def test_sink_distances_vs_scipy_bfs(seed):
     assert (d == expect).all()
 
 
-def test_config0_matches_bruteforce_free_checks():
-    g = I.config0()
+def test_grid2d_64x64_matches_bruteforce_free_checks():
+    g = I.grid2d_64x64()
     r = run_all(g.n, g.s, g.t, g.tail, g.head, g.cap)
     ev, es = oracle.edmonds_karp(g.n, g.s, g.t, g.tail, g.head, g.cap)
     assert r["value"] == ev and (r["cut"] == es).all()
