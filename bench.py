@@ -48,6 +48,18 @@ def model_bytes(st: dict, n: int, m: int) -> int:
                + B_VERTEX_FIXED * n + B_VERTEX_GR * n * st["global_relabels"])
 
 
+def phase_rooflines(st: dict, n: int, peak: float) -> dict:
+    """Algorithmic GB/s of the two parts of the hot path, timed by the kernel's own clock (CTA 0's view of
+    the time spent in discharge rounds and in global relabels, barrier waits included)."""
+    dis = B_SCAN_DIS * st["scans_discharge"] + B_PUSH * st["pushes"] + B_VISIT_DIS * st["visits_discharge"]
+    bfs = B_SCAN_BFS * st["scans_bfs"] + B_VISIT_BFS * st["visits_bfs"] + B_VERTEX_GR * n * st["global_relabels"]
+    out = {}
+    for name, b, ms in (("discharge_rounds", dis, st["discharge_ms"]), ("global_relabel_bfs", bfs, st["relabel_ms"])):
+        gbs = b / (ms * 1e6) if ms > 0 else None
+        out[name] = {"model_bytes": int(b), "ms": ms, "achieved_GBps": gbs, "frac": gbs / peak if gbs else None}
+    return out
+
+
 def apply_overrides(opt, args):
     """Sets the mf_options fields given by --options (a JSON object) on opt."""
     if args.options:
@@ -312,7 +324,8 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": mb / st["solve_ms"] * 1e-6, "peak": peak, "unit": "GB/s",
                          "frac": mb / st["solve_ms"] * 1e-6 / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "mf::solve_kernel", "model_bytes_per_launch": mb,
-                         "scans_per_launch": st["scans_discharge"] + st["scans_bfs"]},
+                         "scans_per_launch": st["scans_discharge"] + st["scans_bfs"],
+                         "phases": phase_rooflines(st, nv, peak)},
             "options": {"tuned": ("cached autotuner choice" if hit else "defaults (no cached choice)")
                         + (f", overridden by {args.options}" if args.options else ""),
                         "use_graph": int(opt.use_graph),
@@ -541,7 +554,8 @@ def main():
         "scans_per_solve": scans / args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "mf::solve_kernel",
-                     "model_bytes_per_launch": statistics.mean(mb)},
+                     "model_bytes_per_launch": statistics.mean(mb),
+                     "phases": phase_rooflines(stats[len(stats) // 2], g.n, peak)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
         "grid": [warm_stats["grid_blocks"], warm_stats["block_threads"]],
         "options": {"tuned": ("cached autotuner choice" if hit else "defaults (no cached choice)")
