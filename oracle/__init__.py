@@ -21,7 +21,11 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 ERRORS = {-1: "invalid argument", -2: "out of memory", -3: "work limit reached",
-          -4: "cut identity failed", -5: "excess left after phase 2"}
+          -4: "cut identity failed", -5: "excess left after phase 2", -6: "invariant failed (checked mode)"}
+
+# checked mode: what the failure code of maxflow_checked means (oracle.c, check_state)
+CHECK_FAILURES = {1: "negative residual", 2: "arc pair capacity not kept", 3: "negative excess",
+                  4: "excess differs from net inflow", 5: "invalid label: d(u) > d(w) + 1 on a residual arc"}
 
 
 def build_lib(force: bool = False) -> str:
@@ -43,6 +47,8 @@ def _L():
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         lib.orc_maxflow.argtypes = [i32, i64, vp, vp, vp, i32, i32, i64, vp, vp, vp]
         lib.orc_maxflow.restype = i64
+        lib.orc_maxflow_checked.argtypes = [i32, i64, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp]
+        lib.orc_maxflow_checked.restype = i64
         lib.orc_edmonds_karp.argtypes = [i32, i64, vp, vp, vp, i32, i32, vp]
         lib.orc_edmonds_karp.restype = i64
         lib.orc_bruteforce_cut.argtypes = [i32, i64, vp, vp, vp, i32, i32, vp]
@@ -92,6 +98,25 @@ def maxflow(n, s, t, tail, head, cap, want_flow=True, want_cut=True, work_limit=
     _check(v)
     return dict(value=int(v), flow=flow, cut=None if cut is None else cut.astype(bool), stats=stats,
                 seconds=sec, truncated=False)
+
+
+def maxflow_checked(n, s, t, tail, head, cap, plant=False):
+    """maxflow with the push-relabel invariants checked after every global relabel, relabel and discharge
+    (residual bounds, pair capacities, excess = net inflow, label validity d(u) <= d(w) + 1 on residual
+    arcs; Section 2.1). plant=True plants a mistake in relabel (one too high) to show that the checker
+    catches it. Returns dict(value or None, cut or None, checks, failed: 0 or the CHECK_FAILURES code)."""
+    tail, head, cap = _i32(tail), _i32(head), _i32(cap)
+    m = tail.shape[0]
+    cut = np.zeros(n, np.uint8)
+    st = np.zeros(8, np.int64)
+    chk = np.zeros(2, np.int64)
+    v = _L().orc_maxflow_checked(n, m, _p(tail), _p(head), _p(cap), s, t, 1 if plant else 0, None, _p(cut),
+                                 _p(st), _p(chk))
+    failed = int(chk[1])
+    if v == -6:
+        return dict(value=None, cut=None, checks=int(chk[0]), failed=failed)
+    _check(v)
+    return dict(value=int(v), cut=cut.astype(bool), checks=int(chk[0]), failed=failed)
 
 
 def edmonds_karp(n, s, t, tail, head, cap):

@@ -38,6 +38,7 @@
 #define ORC_EWORK (-3)     /* work limit reached before the maximum preflow */
 #define ORC_EIDENT (-4)    /* internal: the two cut computations disagree */
 #define ORC_EPHASE2 (-5)   /* internal: excess left after flow reconstruction */
+#define ORC_ECHECK (-6)    /* checked mode: an invariant of push-relabel failed */
 
 typedef struct {
   int32_t n;
@@ -53,6 +54,12 @@ typedef struct {
   uint8_t *inq;   /* n */
   /* statistics */
   int64_t scans, pushes, relabels, grs, work_limit;
+  /* checked mode (orc_maxflow_checked): input capacities, and what failed */
+  const int32_t *cap_in;
+  int check;           /* 0 off, 1 check, 2 check with the planted relabel mistake */
+  int64_t checks;      /* invariant checks run */
+  int32_t check_s;     /* the source s of the instance (its excess may be negative) */
+  int64_t bad;         /* 0, or 1 + the failed invariant (see check_state) */
 } orc_graph;
 
 static void orc_free(orc_graph *g) {
@@ -139,7 +146,8 @@ static void global_relabel(orc_graph *g, int32_t src, int32_t snk) {
   g->grs++;
 }
 
-/* Relabel (Section 2.1): d(v) := 1 + min{ d(w) : (v,w) residual }, at most n. */
+/* Relabel (Section 2.1): d(v) := 1 + min{ d(w) : (v,w) residual }, at most n.
+ * check == 2 plants a mistake (one more than that) for the checker's own test. */
 static void relabel(orc_graph *g, int32_t v) {
   int32_t n = g->n;
   int64_t best = n;
@@ -148,8 +156,44 @@ static void relabel(orc_graph *g, int32_t v) {
     g->scans++;
     if (g->res[a] > 0 && (int64_t)g->d[g->to[a]] + 1 < best) best = (int64_t)g->d[g->to[a]] + 1;
   }
+  if (g->check == 2 && best < n) best++;
   g->d[v] = (int32_t)best;
   g->relabels++;
+}
+
+/* Checked mode: the invariants of a push-relabel phase toward snk (Section
+ * 2.1) on the current state. Returns 0, or the number of the first failure:
+ *   1: a residual is negative;
+ *   2: an arc pair does not keep its capacity (res[a] + res[a^1] = cap);
+ *   3: a vertex other than s holds negative excess;
+ *   4: an excess differs from the net inflow implied by the residuals;
+ *   5: a label is not valid: d(u) > d(w) + 1 for a residual arc (u, w) with
+ *      u other than src (the paper's validity condition for distance labels). */
+static int check_state(orc_graph *g, int32_t s, int32_t src) {
+  const int32_t n = g->n;
+  g->checks++;
+  int64_t *net = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  if (!net) return 0;
+  int fail = 0;
+  for (int64_t i = 0; i < g->m && !fail; i++) {
+    const int64_t f = g->res[2 * i + 1], r = g->res[2 * i];
+    if (r < 0 || f < 0) fail = 1;
+    else if (r + f != (int64_t)g->cap_in[i]) fail = 2;
+    else {
+      net[g->to[2 * i]] += f;      /* head receives f */
+      net[g->to[2 * i + 1]] -= f;  /* tail sends f */
+    }
+  }
+  for (int32_t v = 0; v < n && !fail; v++) {
+    if (v != s && g->e[v] < 0) fail = 3;
+    else if (g->e[v] != net[v]) fail = 4;
+  }
+  for (int64_t a = 0; a < 2 * g->m && !fail; a++) {
+    const int32_t u = g->to[a ^ 1], w = g->to[a];
+    if (u != src && g->res[a] > 0 && (int64_t)g->d[u] > (int64_t)g->d[w] + 1) fail = 5;
+  }
+  free(net);
+  return fail;
 }
 
 /*
@@ -168,6 +212,13 @@ static int pr_phase(orc_graph *g, int32_t src, int32_t snk) {
   for (;;) {
     if (work > thr) {
       global_relabel(g, src, snk);
+      if (g->check) {
+        const int f = check_state(g, g->check_s, src);
+        if (f) {
+          g->bad = f;
+          return ORC_ECHECK;
+        }
+      }
       work = 0;
       qh = 0;
       qcount = 0;
@@ -192,6 +243,13 @@ static int pr_phase(orc_graph *g, int32_t src, int32_t snk) {
     while (g->e[v] > 0) {
       if (g->cur[v] == g->off[v + 1]) {
         relabel(g, v);
+        if (g->check) {  /* after every relabel as well */
+          const int f = check_state(g, g->check_s, src);
+          if (f) {
+            g->bad = f;
+            return ORC_ECHECK;
+          }
+        }
         work += (g->off[v + 1] - g->off[v]) + 12;
         g->cur[v] = g->off[v];
         if (g->d[v] >= n) break;
@@ -214,6 +272,13 @@ static int pr_phase(orc_graph *g, int32_t src, int32_t snk) {
         if (g->res[a] == 0) g->cur[v]++;
       } else {
         g->cur[v]++;
+      }
+    }
+    if (g->check) {  /* after every discharge */
+      const int f = check_state(g, g->check_s, src);
+      if (f) {
+        g->bad = f;
+        return ORC_ECHECK;
       }
     }
   }
@@ -258,13 +323,17 @@ static void residual_reach(orc_graph *g, uint8_t *mark) {
  * phase 1 after about that many arc scans and returns ORC_EWORK (used to time
  * a bounded sample). Returns the flow value (>= 0) or a negative error.
  */
-int64_t orc_maxflow(int32_t n, int64_t m, const int32_t *tail, const int32_t *head, const int32_t *cap, int32_t s,
-                    int32_t t, int64_t work_limit, int64_t *flow_out, uint8_t *cut_out, int64_t *stats) {
+static int64_t maxflow_impl(int32_t n, int64_t m, const int32_t *tail, const int32_t *head, const int32_t *cap,
+                            int32_t s, int32_t t, int64_t work_limit, int64_t *flow_out, uint8_t *cut_out,
+                            int64_t *stats, int check, int64_t *check_out) {
   if (s < 0 || s >= n || t < 0 || t >= n || s == t) return ORC_EINVAL;
   orc_graph g;
   int rc = orc_init(&g, n, m, tail, head, cap);
   if (rc) return rc;
   g.work_limit = work_limit;
+  g.cap_in = cap;
+  g.check = check;
+  g.check_s = s;
   /* initialization: d = 0 except d(s) = n; saturate every arc out of s */
   for (int32_t v = 0; v < n; v++) g.d[v] = 0;
   g.d[s] = n;
@@ -283,6 +352,10 @@ int64_t orc_maxflow(int32_t n, int64_t m, const int32_t *tail, const int32_t *he
     if (stats) {
       int64_t st[8] = {g.scans, g.pushes, g.relabels, g.grs, p1[0], p1[1], p1[2], p1[3]};
       memcpy(stats, st, sizeof(st));
+    }
+    if (check_out) {
+      check_out[0] = g.checks;
+      check_out[1] = g.bad;
     }
     orc_free(&g);
     return rc;
@@ -322,10 +395,33 @@ int64_t orc_maxflow(int32_t n, int64_t m, const int32_t *tail, const int32_t *he
     int64_t st[8] = {g.scans, g.pushes, g.relabels, g.grs, p1[0], p1[1], p1[2], p1[3]};
     memcpy(stats, st, sizeof(st));
   }
+  if (check_out) {
+    check_out[0] = g.checks;
+    check_out[1] = g.bad;
+  }
   free(r);
   free(smin);
   orc_free(&g);
   return rc == ORC_OK ? value : rc;
+}
+
+int64_t orc_maxflow(int32_t n, int64_t m, const int32_t *tail, const int32_t *head, const int32_t *cap, int32_t s,
+                    int32_t t, int64_t work_limit, int64_t *flow_out, uint8_t *cut_out, int64_t *stats) {
+  return maxflow_impl(n, m, tail, head, cap, s, t, work_limit, flow_out, cut_out, stats, 0, NULL);
+}
+
+/*
+ * orc_maxflow in checked mode: after every global relabel, relabel and
+ * discharge of both phases the state is checked (check_state: residual bounds, pair
+ * capacities, excess = net inflow, label validity). plant = 1 plants a
+ * mistake in relabel (one too high), so that a test can see the checker
+ * catch it. check_out (2 entries) = {checks run, 0 or 1 + failed invariant}.
+ * Returns as orc_maxflow, or ORC_ECHECK when an invariant failed.
+ */
+int64_t orc_maxflow_checked(int32_t n, int64_t m, const int32_t *tail, const int32_t *head, const int32_t *cap,
+                            int32_t s, int32_t t, int32_t plant, int64_t *flow_out, uint8_t *cut_out,
+                            int64_t *stats, int64_t *check_out) {
+  return maxflow_impl(n, m, tail, head, cap, s, t, 0, flow_out, cut_out, stats, plant ? 2 : 1, check_out);
 }
 
 /*

@@ -263,3 +263,37 @@ def test_networkx_maximum_flow(seed):
             G.add_edge(u, v, capacity=c)
     r = run_all(g.n, g.s, g.t, g.tail, g.head, g.cap)
     assert r["value"] == nx.maximum_flow_value(G, g.s, g.t)
+
+
+CHECKED_CASES = {
+    "random": lambda k: I.random_graph(24 + 3 * k, 200 + 40 * k, 500 + k, cap=(1, 60)),
+    "grid2d": lambda k: I.grid2d(8 + k, 9, 510 + k),
+    "grid3d": lambda k: I.grid3d(5, 6, 4 + k, 520 + k),
+    "layered": lambda k: I.layered(5 + k, 12, 530 + k),
+    "rmat": lambda k: I.rmat(7, 6, 540 + k),
+    "multiframe": lambda k: I.multiframe(3, 550 + k, side=6),
+}
+
+
+@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("family", sorted(CHECKED_CASES))
+def test_invariants_hold_after_every_relabel_and_discharge(family, k):
+    """Checked mode (Section 2.1 invariants after every global relabel, relabel and discharge, both phases):
+    no invariant fails, and the value and S_min equal those of the unchecked oracle and of Edmonds-Karp."""
+    g = CHECKED_CASES[family](k)
+    r = oracle.maxflow_checked(g.n, g.s, g.t, g.tail, g.head, g.cap)
+    assert r["failed"] == 0, oracle.CHECK_FAILURES.get(r["failed"])
+    assert r["checks"] > 0
+    plain = oracle.maxflow(g.n, g.s, g.t, g.tail, g.head, g.cap, want_flow=False)
+    assert r["value"] == plain["value"] and np.array_equal(r["cut"], plain["cut"])
+    v, cut = oracle.edmonds_karp(g.n, g.s, g.t, g.tail, g.head, g.cap)
+    assert r["value"] == v and np.array_equal(r["cut"], cut)
+
+
+@pytest.mark.parametrize("family", ["random", "grid2d", "grid3d", "layered"])
+def test_checked_mode_catches_a_planted_relabel_mistake(family):
+    """A relabel one too high breaks label validity (d(u) <= d(w) + 1 on residual arcs); the checker must
+    report exactly that."""
+    g = CHECKED_CASES[family](1)
+    r = oracle.maxflow_checked(g.n, g.s, g.t, g.tail, g.head, g.cap, plant=True)
+    assert r["value"] is None and r["failed"] == 5, (r["failed"], r["value"])
