@@ -130,6 +130,12 @@ typedef struct mf_options {
    * at the end are the exact BFS distances either way). 1: one level per
    * barrier, as Algorithm 2. Default 8; range [1, 64]. */
   int32_t bfs_hops;
+  /* Gap relabeling every gap_every rounds (0 = off, the default): when no
+   * vertex has some label g below n, every vertex with a label between g and
+   * n cannot reach the sink and gets label n (Section 2.1's gap heuristic,
+   * which the paper's parallel code leaves out). Single-instance graphs with
+   * the improved rounds only (no effect on batches and simple_rounds). */
+  int32_t gap_every;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
@@ -155,6 +161,7 @@ typedef struct mf_stats {
   double round_work_ms, round_tail_ms, round_wait_ms, level_work_ms, level_wait_ms;
   int32_t grid_blocks;      /* persistent-kernel CTAs */
   int32_t block_threads;
+  int64_t gap_lifted;       /* vertices lifted to label n by gap relabeling */
 } mf_stats;
 
 typedef struct mf_graph mf_graph;

@@ -124,8 +124,8 @@ static int flags_to_status(unsigned f) {
 // ------------------------------------------------------------------ graph
 
 static void free_graph_buffers(mf_graph *g) {
-  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab,
-                g->list[0], g->list[1], g->list[2], g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap};
+  void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab, g->list[0], g->list[1], g->list[2],
+                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap, g->hist};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
@@ -247,6 +247,7 @@ int check_options(const mf_options *o) {
   if (!(o->gr_time_ratio >= 0)) return fail(MF_ERR_INVALID_ARG, "gr_time_ratio must be >= 0");
   if (o->use_graph != 0 && o->use_graph != 1) return fail(MF_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   if (o->bfs_hops < 1 || o->bfs_hops > 64) return fail(MF_ERR_INVALID_ARG, "bfs_hops must be in [1, 64]");
+  if (o->gap_every < 0) return fail(MF_ERR_INVALID_ARG, "gap_every must be >= 0");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
@@ -289,6 +290,8 @@ Dev make_dev(const mf_graph *g) {
   D.cta_vertices = g->max_degree > (long long)g->opt.bin_warp ? 1 : 0;
   D.keep_local = keep_local_limit(g->opt, g->max_degree, g->block);
   D.bfs_hops = D.keep_local > 0 ? g->opt.bfs_hops : 1;
+  D.gap_every = (g->ninst == 1 && !D.simple && g->hist) ? g->opt.gap_every : 0;
+  D.hist = g->hist;
   D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
@@ -344,6 +347,13 @@ static int ensure_graph(mf_graph *g, const Dev &D, cudaStream_t st) {
 // Runs the persistent kernel once with D; fills g->h_ctl and g->stats.
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   cudaError_t e;
+  if (g->opt.gap_every > 0 && g->ninst == 1 && !g->opt.simple_rounds && !g->hist) {
+    // label counts for gap relabeling, zeroed by the kernel before use
+    if ((e = cudaMalloc((void **)&g->hist, ((size_t)g->n_cap + 1) * sizeof(int))) != cudaSuccess)
+      return cuda_fail(e, "cudaMalloc label counts");
+    D.hist = g->hist;
+    D.gap_every = g->opt.gap_every;
+  }
   if (g->opt.use_graph && st != nullptr) {
     const int rc = ensure_graph(g, D, st);
     if (rc) return rc;
@@ -382,12 +392,13 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   s.preflow_ms = c.t_preflow > c.t_start ? (double)(c.t_preflow - c.t_start) * 1e-6 : 0.0;
   s.grid_blocks = g->grid;
   s.block_threads = g->block;
+  s.gap_lifted = c.gap_lifted;
   if (c.err) {
     static const char *where[] = {"init barrier", "saturation barrier", "relabel BFS", "working-set rebuild",
                                   "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
                                   "phase-2 excess check", "cut BFS", "round limit", "list capacity",
-                                  "settle barrier"};
-    const char *w = (c.err_where >= 0 && c.err_where <= 12) ? where[c.err_where] : "?";
+                                  "settle barrier", "gap relabeling"};
+    const char *w = (c.err_where >= 0 && c.err_where <= 13) ? where[c.err_where] : "?";
     if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
     if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);
     if (c.err == MF_ERR_INTERNAL && c.err_where == 8)

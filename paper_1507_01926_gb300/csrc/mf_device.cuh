@@ -37,6 +37,8 @@ struct Ctl {
   long long rounds_by_size[4];               // rounds with <1K, <16K, <256K, more list entries
   unsigned long long t_start, t_preflow, t_end;  // %globaltimer, ns
   int stopped_round;   // MODE_ROUNDS: rounds run
+  int gap;             // gap relabeling: smallest label without a vertex (INT_MAX: none found yet)
+  long long gap_lifted;  // vertices lifted to the label cap by gap relabeling
 };
 // the kernel reads cnt as one int4 and gr_req as one int2
 static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, lcnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0,
@@ -75,6 +77,8 @@ struct Dev {
   unsigned long long *blab;  // n: BFS words {label, flags} (dense, so that BFS gathers stay in L2); the rebuild
                              // copies the labels into both label slots
   int bfs_hops;      // BFS levels a CTA may expand per grid barrier (1: one level per barrier)
+  int gap_every;     // gap relabeling every this many rounds (0: off; single instance, improved rounds only)
+  int *hist;         // n + 1 label counts for gap relabeling (zero between uses), or nullptr
   int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance

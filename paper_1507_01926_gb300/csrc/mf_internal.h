@@ -26,6 +26,7 @@ struct mf_graph {
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
   int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)
+  int *hist = nullptr;         // label counts for gap relabeling (allocated on first use)
   mf::Ctl *ctl = nullptr;
   long long *d_value = nullptr;
   int *d_flow = nullptr;

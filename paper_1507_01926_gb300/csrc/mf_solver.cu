@@ -1284,6 +1284,46 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
   return true;
 }
 
+// Gap relabeling (Section 2.1 names the heuristic; the paper's parallel code
+// leaves it out). Between two rounds, with the labels the next round reads in
+// slot p: if no vertex has label g (0 < g < cap) while some have larger
+// labels below the cap, none of those can reach the sink: a residual path
+// from such a vertex passes labels that drop by at most one per arc (valid
+// labels), so it would pass label g. They get the cap in both slots, which
+// keeps the labels valid. Three grid barriers: count labels, find the
+// smallest empty label, lift. Single-instance graphs only (one label range).
+__device__ bool gap_relabel(const Dev &D, Shared &sh, int p) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int cap = D.n_cap;
+  if (tid == 0) D.ctl->gap = INT_MAX;
+  for (int v = tid; v < D.n; v += nthr) {
+    const int d = __ldcg(lab_ptr(D, v, p));
+    if (d >= 1 && d < cap) atomicAdd(&D.hist[d], 1);
+  }
+  if (!grid_sync(D, sh, 13)) return false;
+  for (int k = 1 + tid; k < cap; k += nthr)
+    if (__ldcg(&D.hist[k]) == 0) {
+      atomicMin(&D.ctl->gap, k);
+      break;  // this thread's later k are larger
+    }
+  if (!grid_sync(D, sh, 13)) return false;
+  const int g = vol_read(&D.ctl->gap);
+  long long lifted = 0;
+  if (g < cap)
+    for (int v = tid; v < D.n; v += nthr) {
+      const int d = __ldcg(lab_ptr(D, v, p));
+      if (d > g && d < cap) {
+        *lab_ptr(D, v, 0) = cap;
+        *lab_ptr(D, v, 1) = cap;
+        lifted++;
+      }
+    }
+  for (int k = tid; k <= cap; k += nthr) D.hist[k] = 0;
+  lifted = block_sum(lifted, sh);
+  if (threadIdx.x == 0 && lifted) atomic_add64(&D.ctl->gap_lifted, lifted);
+  return grid_sync(D, sh, 13);
+}
+
 // Ends a MODE_ROUNDS run between rounds: every vertex gets its current label
 // (slot p) in both slots and its addedExcess folded into its excess.
 __device__ bool settle(const Dev &D, Shared &sh, int p) {
@@ -1368,6 +1408,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       D.ctl->rounds++;
       if (phase1) D.ctl->rounds_phase1++;
     }
+    if (D.gap_every > 0 && rounds % D.gap_every == 0 && !gap_relabel(D, sh, r & 1)) return false;
   }
   if (D.mode == MODE_ROUNDS) {
     if (timer) D.ctl->stopped_round = (int)rounds;
@@ -1405,6 +1446,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
     reinterpret_cast<int4 *>(D.vs + v)[0] = make_int4(0, -1, 0, -1);
     reinterpret_cast<longlong2 *>(D.vs + v)[1] = make_longlong2(0, 0);
   }
+  if (D.gap_every > 0)
+    for (int k = tid; k <= D.n_cap; k += nthr) D.hist[k] = 0;
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
   if (ok) {
