@@ -79,25 +79,31 @@ __global__ void k_check_slots(int n, long long m, const int *head, const int *ca
   if (f) atomicOr(flags, f);
 }
 
-__global__ void k_check_pairs(int n, long long m, const int *row, const int *head, const int *cap, const int *rev,
-                              unsigned *flags, unsigned long long *m_arcs) {
+// Pairing checks, one warp per vertex v (the row gives every slot's tail, so
+// no search is needed): rev[rev[a]] = a, head[rev[a]] = v, and the pair's
+// capacities fit int32; counts the slots with positive capacity.
+__global__ void k_check_pairs(int n, const int *row, const int *head, const int *cap, const int *rev, unsigned *flags,
+                              unsigned long long *m_arcs) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   unsigned f = 0;
   unsigned long long cnt = 0;
-  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m; a += (long long)gridDim.x * blockDim.x) {
-    // tail(a): last v with row[v] <= a
-    int lo = 0, hi = n;  // row[lo] <= a < row[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (row[mid] <= a) lo = mid; else hi = mid;
+  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int b = row[v], e = row[v + 1];
+    for (int a = b + lane; a < e; a += 32) {
+      const int ra = rev[a];
+      if (rev[ra] != a) f |= V_PAIR;
+      if (head[ra] != (int)v) f |= V_TAIL;
+      if ((long long)cap[a] + (long long)cap[ra] > 2147483647LL) f |= V_OVERFLOW;
+      if (cap[a] > 0) cnt++;
     }
-    const int ra = rev[a];
-    if (rev[ra] != (int)a) f |= V_PAIR;
-    if (head[ra] != lo) f |= V_TAIL;
-    if ((long long)cap[a] + (long long)cap[ra] > 2147483647LL) f |= V_OVERFLOW;
-    if (cap[a] > 0) cnt++;
   }
-  if (f) atomicOr(flags, f);
-  if (cnt) atomicAdd(m_arcs, cnt);
+  f = __reduce_or_sync(0xffffffffu, f);
+  cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+  if (lane == 0) {
+    if (f) atomicOr(flags, f);
+    if (cnt) atomicAdd(m_arcs, cnt);
+  }
 }
 
 // Largest out-degree (slots) of a vertex other than s and t.
@@ -206,7 +212,9 @@ int validate_on_device(mf_graph *g, const long long *row64, const long long *rev
     return cuda_fail(e, "graph validation");
   }
   if (h[0] == 0 && g->m > 0) {
-    k_check_pairs<<<Gm, T, 0, st>>>(g->n, g->m, g->row, g->head, g->cap, g->rev, flags, marcs);
+    const long long gw = ((long long)g->n * 32 + T - 1) / T;  // one warp per vertex
+    const int Gw = (int)(gw < 65535LL * 16 ? gw : 65535LL * 16);
+    k_check_pairs<<<Gw, T, 0, st>>>(g->n, g->row, g->head, g->cap, g->rev, flags, marcs);
     k_max_degree<<<Gn, T, 0, st>>>(g->n, g->row, g->s, g->t, flags + 1);
     e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
