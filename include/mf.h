@@ -136,6 +136,12 @@ typedef struct mf_options {
    * which the paper's parallel code leaves out). Single-instance graphs with
    * the improved rounds only (no effect on batches and simple_rounds). */
   int32_t gap_every;
+  /* Direction-optimizing BFS: a level of a level-synchronous BFS (bfs_hops
+   * 1 or the CTA-local lists not active) whose frontier holds more than
+   * n / bfs_pull vertices runs bottom-up: every vertex not reached yet scans
+   * its own arcs for one into the frontier and stops at the first. Same
+   * labels. Default 50; 0 = always top-down. */
+  int32_t bfs_pull;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
@@ -286,8 +292,8 @@ void mf_batch_destroy(mf_batch *b);
  * gr_freq {0.25, 0.5, 1, 2}, bin_thread {2, 4, 8, 16}, bin_warp {128, 1024, 8192},
  * the launch shape (threads per CTA, CTAs per SM) {(256, 2), (512, 1),
  * (128, 4), (256, 1)}, kernel_variant {0..4} (and variant 4 with
- * bin_thread 16), local_lists {0, 1} and
- * bfs_hops {1, 4, 8, 16} (the last two only on graphs where they act),
+ * bin_thread 16), local_lists {0, 1}, bfs_hops {1, 4, 8, 16} (these two
+ * only on graphs where they act) and bfs_pull {0, 20, 50, 200},
  * starting from g's current options; candidates that are invalid together or
  * do not fit the GPU are skipped. A candidate's time is the median device time of spec->reps solves
  * (maximum flow value only, no per-arc outputs); spec->sweeps passes over the

@@ -256,6 +256,7 @@ int check_options(const mf_options *o) {
   if (o->use_graph != 0 && o->use_graph != 1) return fail(MF_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   if (o->bfs_hops < 1 || o->bfs_hops > 64) return fail(MF_ERR_INVALID_ARG, "bfs_hops must be in [1, 64]");
   if (o->gap_every < 0) return fail(MF_ERR_INVALID_ARG, "gap_every must be >= 0");
+  if (o->bfs_pull < 0) return fail(MF_ERR_INVALID_ARG, "bfs_pull must be >= 0");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
@@ -299,6 +300,7 @@ Dev make_dev(const mf_graph *g) {
   D.keep_local = keep_local_limit(g->opt, g->max_degree, g->block);
   D.bfs_hops = D.keep_local > 0 ? g->opt.bfs_hops : 1;
   D.gap_every = (g->ninst == 1 && !D.simple && g->hist) ? g->opt.gap_every : 0;
+  D.bfs_pull = g->opt.bfs_pull;
   D.hist = g->hist;
   D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
@@ -440,6 +442,7 @@ void mf_default_options(mf_options *o) {
   o->gr_time_ratio = 2.0;
   o->local_lists = 1;
   o->bfs_hops = 8;
+  o->bfs_pull = 50;
 }
 
 const char *mf_last_error(void) { return last_error(); }

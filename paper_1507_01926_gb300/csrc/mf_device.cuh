@@ -78,6 +78,7 @@ struct Dev {
                              // copies the labels into both label slots
   int bfs_hops;      // BFS levels a CTA may expand per grid barrier (1: one level per barrier)
   int gap_every;     // gap relabeling every this many rounds (0: off; single instance, improved rounds only)
+  int bfs_pull;      // bottom-up BFS levels when the frontier exceeds n / bfs_pull vertices (0: never)
   int *hist;         // n + 1 label counts for gap relabeling (zero between uses), or nullptr
   int *list[3];      // vertex lists, generation g uses list[g % 3]
   const int *src;    // sources (phase 1), one per instance

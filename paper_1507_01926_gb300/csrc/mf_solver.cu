@@ -1177,6 +1177,85 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
   phase_end(D, sh, next, 0, nullptr);
 }
 
+// One bottom-up level (direction-optimizing BFS, Beamer, Asanovic and Patterson
+// 2012) for a level-synchronous BFS whose frontier is large: every vertex w not
+// reached yet looks for a residual arc to a vertex labelled `depth` and takes
+// depth + 1 at the first one, instead of the frontier offering labels along all
+// its arcs. Same labels as the top-down level: w is reached at depth + 1 iff
+// such an arc exists. Slot a of w's row is (w -> v); the reverse BFS (global
+// relabel) needs c_f(w, v) = res[a], the forward BFS (cut) c_f(v, w) =
+// res[rev[a]]. Thread per vertex up to 32 slots, warp per vertex above.
+__device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int depth, bool reverse, TStat &st) {
+  const int next = gen + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
+  }
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < D.n; base += stride) {
+    const long long wl = base + threadIdx.x;
+    const int w = wl < D.n ? (int)wl : -1;
+    int beg = 0, deg = 0;
+    bool open = false;
+    if (w >= 0) {
+      const unsigned long long x = __ldcg(D.blab + w);
+      open = (int)(x >> 32) == UNV && !(x & BB);
+      if (open) {
+        beg = __ldg(&D.row[w]);
+        deg = __ldg(&D.row[w + 1]) - beg;
+        open = deg > 0;
+      }
+    }
+    if (open && deg <= 32) {  // thread per vertex, stop at the first arc into the level
+      for (int i = 0; i < deg; i++) {
+        st.scans_bfs++;
+        const int2 r = __ldcg(&D.rr[beg + i]);
+        if ((reverse ? r.x : r.y) <= 0) continue;
+        const unsigned long long y = __ldcg(D.blab + __ldg(&D.head[beg + i]));
+        if ((int)(y >> 32) == depth && !(y & BB)) {
+          D.blab[w] = bword(depth + 1, BQ);
+          st.visits_bfs++;
+          qpush(D, sh, next, w);
+          break;
+        }
+      }
+      open = false;
+    }
+    for (;;) {  // warp per vertex
+      const unsigned mm = __ballot_sync(FULL, open);
+      if (!mm) break;
+      const int leader = __ffs(mm) - 1;
+      const int pw = __shfl_sync(FULL, w, leader);
+      const int pb = __shfl_sync(FULL, beg, leader);
+      const int pd = __shfl_sync(FULL, deg, leader);
+      if (lane == leader) open = false;
+      for (int c = 0; c < pd; c += 32) {
+        bool hit = false;
+        if (c + lane < pd) {
+          st.scans_bfs++;
+          const int a = pb + c + lane;
+          const int2 r = __ldcg(&D.rr[a]);
+          if ((reverse ? r.x : r.y) > 0) {
+            const unsigned long long y = __ldcg(D.blab + __ldg(&D.head[a]));
+            hit = (int)(y >> 32) == depth && !(y & BB);
+          }
+        }
+        if (__ballot_sync(FULL, hit)) {
+          if (lane == 0) {
+            D.blab[pw] = bword(depth + 1, BQ);
+            st.visits_bfs++;
+            qpush(D, sh, next, pw);
+          }
+          break;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  phase_end(D, sh, next, 0, nullptr);
+}
+
 // BFS from `seeds` (label 0) over blab. `blockers` are never entered. With
 // `excess_seeds`, every vertex holding excess whose label lies in [1, cap] is
 // a seed as well (cut from the maximum preflow). Returns false on error. On
@@ -1214,7 +1293,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   if (!grid_sync(D, sh, where)) return false;
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-  for (;;) {
+  for (int depth = 0;; depth++) {
     const long long fcount = gen_total(D, sh, gen);
     if (fcount == 0) break;
     if (timer && D.trace_lv) {
@@ -1222,7 +1301,12 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
       if (k < D.trace_lv_cap) D.trace_lv[k] = (int)fcount;
     }
     const unsigned long long t0 = timer ? gtimer() : 0;
-    bfs_level<KTD>(D, sh, gen, reverse, st);
+    // bottom-up when the frontier holds more than n / bfs_pull vertices (only for level-synchronous
+    // BFS, where every frontier vertex carries the label `depth`)
+    if (D.bfs_pull > 0 && D.bfs_hops == 1 && fcount * D.bfs_pull > D.n)
+      bfs_pull_level(D, sh, gen, depth, reverse, st);
+    else
+      bfs_level<KTD>(D, sh, gen, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
     if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
     gen++;

@@ -52,7 +52,7 @@ int measure(mf_graph *g, int reps, double *median_ms, std::vector<long long> *va
   return MF_OK;
 }
 
-enum Coord { GR_TIME_RATIO, GR_FREQ, BIN_THREAD, BIN_WARP, SHAPE, VARIANT, LOCAL, HOPS, NCOORD };
+enum Coord { GR_TIME_RATIO, GR_FREQ, BIN_THREAD, BIN_WARP, SHAPE, VARIANT, LOCAL, HOPS, PULL, NCOORD };
 
 const double kTimeRatio[] = {0.0, 1.0, 2.0, 4.0};
 const double kFreq[] = {0.25, 0.5, 1.0, 2.0};
@@ -65,6 +65,7 @@ const int kShape[][2] = {{256, 2}, {512, 1}, {128, 4}, {256, 1}};  // threads pe
 const int kVariant[][2] = {{0, -1}, {1, -1}, {2, -1}, {3, -1}, {4, -1}, {4, 16}};
 const int kLocal[] = {0, 1};            // CTA-local lists off / on (K = block_threads / 2)
 const int kHops[] = {1, 4, 8, 16};      // BFS levels per grid barrier
+const int kPull[] = {0, 20, 50, 200};    // bottom-up BFS levels above n / bfs_pull frontier vertices
 
 int candidates(Coord c) {
   switch (c) {
@@ -76,6 +77,7 @@ int candidates(Coord c) {
     case VARIANT: return 6;
     case LOCAL: return 2;
     case HOPS: return 4;
+    case PULL: return 4;
     default: return 0;
   }
 }
@@ -97,6 +99,7 @@ mf_options with(const mf_options &o, Coord c, int k) {
       break;
     case LOCAL: x.local_lists = kLocal[k]; break;
     case HOPS: x.bfs_hops = kHops[k]; break;
+    case PULL: x.bfs_pull = kPull[k]; break;
     default: break;
   }
   return x;

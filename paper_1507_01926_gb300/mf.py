@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int32),
                 ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32), ("gr_time_ratio", ctypes.c_double),
                 ("kernel_variant", ctypes.c_int32), ("simple_rounds", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("local_lists", ctypes.c_int32), ("bfs_hops", ctypes.c_int32), ("gap_every", ctypes.c_int32)]
+                ("local_lists", ctypes.c_int32), ("bfs_hops", ctypes.c_int32), ("gap_every", ctypes.c_int32),
+                ("bfs_pull", ctypes.c_int32)]
 
 
 class TuneSpec(ctypes.Structure):

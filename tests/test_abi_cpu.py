@@ -133,12 +133,12 @@ def test_create_graph_argument_errors_without_gpu(built):
 
 @pytest.mark.parametrize("field,bad", [("use_graph", 2), ("local_lists", -1), ("local_lists", 16), ("local_lists", 1024),
                                        ("bfs_hops", 0), ("bfs_hops", 65), ("bin_thread", 16), ("bin_thread", 17),
-                                       ("kernel_variant", 5), ("gap_every", -1)])
+                                       ("kernel_variant", 5), ("gap_every", -1), ("bfs_pull", -1)])
 def test_out_of_range_options_rejected_without_gpu(built, field, bad):
     from paper_1507_01926_gb300 import mf
 
     o = mf.default_options()
-    assert (o.use_graph, o.local_lists, o.bfs_hops) == (0, 1, 8)
+    assert (o.use_graph, o.local_lists, o.bfs_hops, o.gap_every, o.bfs_pull) == (0, 1, 8, 0, 50)
     z32, z64 = np.zeros(0, np.int32), np.zeros(0, np.int64)
     with pytest.raises(mf.MFError) as e:
         mf.Graph(3, np.zeros(4, np.int64), z32, z32, z64, 0, 2, mf.default_options(**{field: bad}))

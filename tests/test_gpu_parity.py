@@ -265,7 +265,8 @@ def test_trace_matches_stats(gpu, hops):
     CTAs also expand vertices they reached within the level, so the frontiers add up to at most that."""
     g = I.grid3d(30, 30, 16, seed=9)
     csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
-    with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(bfs_hops=hops)) as G:
+    # (bottom-up levels count the vertices they reach, not the frontier: off here)
+    with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(bfs_hops=hops, bfs_pull=0)) as G:
         live, gr, levels = G.solve_trace()
         st = G.stats()
     assert len(live) == st["rounds"] and len(levels) == st["bfs_levels"]
