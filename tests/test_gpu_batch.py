@@ -78,3 +78,12 @@ def test_batch_rejects_bad_instance(gpu):
     with pytest.raises(gpu.MFError) as e:
         gpu.Batch([c], [(good.s, good.s)])
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("hops", [1, 8, 32])
+def test_batch_of_grids_local_lists_and_hops(gpu, hops):
+    """A batch whose instances are all grids (every vertex thread-sized): the CTA-local lists and the
+    label-correcting BFS act across instances; each instance must still get the oracle's value and S_min."""
+    insts = [I.grid2d(20 + 7 * k, 30 + 3 * k, 800 + k) for k in range(5)]
+    insts += [I.grid3d(10 + k, 9, 6 + k, 810 + k) for k in range(3)] + [I.multiframe(3, 820, side=24)]
+    check_batch(gpu, insts, gpu.default_options(bfs_hops=hops))
