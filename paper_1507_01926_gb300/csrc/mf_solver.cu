@@ -13,8 +13,8 @@
 // during round r + 1, where they touch nothing that round reads.
 //
 // Data model (mf_device.cuh): CSR of paired slots with an inline copy of the
-// reverse residual (int2 rr[a] = {res[a], res[rev[a]]}, the "each edge also
-// stores the residual capacity of its reverse edge" layout of Section 4.2),
+// reverse residual (int2 rr[a] = {res[a], res[rev[a]]}: the residual of an
+// arc's reverse is kept next to the arc, as in the paper's layout, Section 4.2),
 // per-vertex {label, active stamp} slots by round parity, int64 excess.
 // Vertex lists are plain arrays filled by warp-aggregated atomics; a list is
 // consumed in tiles of blockDim entries that are binned in shared memory by
