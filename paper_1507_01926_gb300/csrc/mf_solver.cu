@@ -21,8 +21,8 @@
 // degree (thread / warp / CTA per vertex).
 //
 // Readings of the listing that the kernel follows (Algorithm 1):
-//  * the activity test of a neighbour w ("if e(w)") is membership of w in the
-//    current working set, kept as a round stamp;
+//  * the activity test of a neighbour w (a test of its excess) is membership
+//    of w in the current working set, kept as a round stamp;
 //  * pushes use the local excess of the discharging vertex;
 //  * excess received by a vertex of the working set goes to its addedExcess
 //    (atomic), excess received by any other vertex is added to its excess
