@@ -353,9 +353,11 @@ def run_serve(args):
     prep_s = time.perf_counter() - t0
     budget = 64 << 30
 
+    sopt = apply_overrides(mf.default_options(device=0), args)
+
     def run(rate):
         arrivals = [a / rate for a, _, _ in reqs] if rate else [0.0] * len(reqs)
-        with mf.Service(budget) as svc:
+        with mf.Service(budget, sopt) as svc:
             t_start = time.perf_counter()
             tickets = []
             for (g, c), at in zip(items, arrivals):
@@ -383,7 +385,7 @@ def run_serve(args):
             "ms_per_step": 1000.0 / out["0.7X"]["solves_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
             "config": {"workload": f"first {len(reqs)} requests of the 2D-grid / multi-frame stream", "vertices": nv,
-                       "budget_bytes": budget},
+                       "budget_bytes": budget, "options": args.options or "defaults"},
             "latency": out, "host_prep_s": prep_s}
     print(json.dumps(line), flush=True)
     return 0

@@ -323,10 +323,12 @@ int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, d
 
 /*
  * Serving with continuous batching. mf_service_create starts worker lanes on
- * opt->device (each lane: a host thread, a CUDA stream and a share of the
- * SMs). mf_submit copies the instance (host arrays, paired-slot CSR) and
- * returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
- * exceed device_budget_bytes (its estimated device footprint is 61 bytes per
+ * opt->device (each lane: a host thread, a CUDA stream and one CTA of
+ * opt->block_threads threads on every SM for its persistent launches; as many
+ * lanes as such CTAs fit an SM, at most 8 and at most opt->blocks_per_sm when
+ * that is set). mf_submit copies the instance (host arrays, paired-slot CSR)
+ * and returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
+ * exceed device_budget_bytes (its estimated device footprint is 65 bytes per
  * vertex + 32 bytes per slot). Lanes admit queued requests in arrival order
  * while the resident footprint stays within the budget, solve each admitted
  * group in one persistent launch, and keep the results. A request that

@@ -55,7 +55,7 @@ size_t footprint(long long n, long long m) { return (size_t)(65 * n + 32 * m + 6
 struct mf_service {
   size_t budget = 0;
   mf_options opt{};
-  int lanes = 2;
+  int lanes = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request *> pending;
@@ -176,8 +176,11 @@ int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_serv
     return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", o.block_threads);
   mf_service *svc = new mf_service();
   svc->budget = device_budget_bytes;
-  svc->lanes = bps >= 2 ? 2 : 1;
-  o.blocks_per_sm = bps / svc->lanes;  // each lane's launches take its share of every SM
+  // one lane per CTA slot of an SM (at most 8): a lane's launch takes one CTA per SM, so the lanes'
+  // persistent kernels are resident together and the requests of different lanes overlap on the device
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
+  svc->lanes = bps < 8 ? bps : 8;
+  o.blocks_per_sm = 1;
   svc->opt = o;
   for (int k = 0; k < svc->lanes; k++) svc->workers.emplace_back(lane_main, svc, k);
   *out = svc;
