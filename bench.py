@@ -379,6 +379,11 @@ def run_serve(args):
         assert vals == vals0
         out[f"{frac:.1f}X"] = {"rate_per_s": frac * X, "solves_per_s": len(reqs) / wall,
                                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    for rate in args.rates:  # fixed arrival rates, for comparing policies at the same load
+        lat, wall, vals = run(rate)
+        assert vals == vals0
+        out[f"{rate:g}/s"] = {"rate_per_s": rate, "solves_per_s": len(reqs) / wall,
+                              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
     nv = sum(g.n for g, _ in items)
     line = {"metric": "served solves/s with p50/p99 latency (Poisson stream)", "value": out["0.7X"]["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
@@ -406,6 +411,7 @@ def main():
     ap.add_argument("--plain-count", type=int, default=128)
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--no-graph", action="store_true", help="batch workload: launch directly, no CUDA graphs")
+    ap.add_argument("--rates", type=float, nargs="*", default=[], help="serve workload: extra fixed arrival rates")
     ap.add_argument("--options", default="", help="JSON object of mf_options fields applied over the chosen options")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -142,6 +142,9 @@ typedef struct mf_options {
    * its own arcs for one into the frontier and stops at the first. Same
    * labels. Default 50; 0 = always top-down. */
   int32_t bfs_pull;
+  /* Serving: most requests a lane packs into one persistent launch (0 = as
+   * many as are queued and fit the budget, the default). */
+  int32_t union_max_requests;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a

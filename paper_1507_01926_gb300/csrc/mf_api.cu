@@ -257,6 +257,7 @@ int check_options(const mf_options *o) {
   if (o->bfs_hops < 1 || o->bfs_hops > 64) return fail(MF_ERR_INVALID_ARG, "bfs_hops must be in [1, 64]");
   if (o->gap_every < 0) return fail(MF_ERR_INVALID_ARG, "gap_every must be >= 0");
   if (o->bfs_pull < 0) return fail(MF_ERR_INVALID_ARG, "bfs_pull must be >= 0");
+  if (o->union_max_requests < 0) return fail(MF_ERR_INVALID_ARG, "union_max_requests must be >= 0");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())

@@ -93,6 +93,7 @@ static void lane_main(mf_service *svc, int lane) {
       if (svc->stop) break;
       long long nn = 0, mm = 0;
       while (!svc->pending.empty()) {
+        if (o.union_max_requests > 0 && (int)batch.size() >= o.union_max_requests) break;
         Request *r = svc->pending.front();
         if (svc->in_use + bytes + r->bytes > svc->budget) break;
         if (svc->resident_n + nn + r->n > UNV - 4 || svc->resident_m + mm + r->m > 2147483646LL) break;

@@ -133,7 +133,8 @@ def test_create_graph_argument_errors_without_gpu(built):
 
 @pytest.mark.parametrize("field,bad", [("use_graph", 2), ("local_lists", -1), ("local_lists", 16), ("local_lists", 1024),
                                        ("bfs_hops", 0), ("bfs_hops", 65), ("bin_thread", 16), ("bin_thread", 17),
-                                       ("kernel_variant", 5), ("gap_every", -1), ("bfs_pull", -1)])
+                                       ("kernel_variant", 5), ("gap_every", -1), ("bfs_pull", -1),
+                                       ("union_max_requests", -1)])
 def test_out_of_range_options_rejected_without_gpu(built, field, bad):
     from paper_1507_01926_gb300 import mf
 
