@@ -201,7 +201,13 @@ typedef struct mf_graph_desc {
   int32_t s, t;
 } mf_graph_desc;
 
+/* Fills *opt with the defaults documented at each field. */
 void mf_default_options(mf_options *opt);
+
+/* Sizes in bytes of mf_options and mf_stats as this library was built, so
+ * that a binding can check its copies of the two structs (either pointer
+ * nullable). No counterpart in the paper. */
+void mf_struct_sizes(int32_t *options_bytes, int32_t *stats_bytes);
 
 /* Last error message of the calling thread ("" if none). */
 const char *mf_last_error(void);

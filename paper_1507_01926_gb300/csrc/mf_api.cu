@@ -448,6 +448,11 @@ void mf_default_options(mf_options *o) {
 
 const char *mf_last_error(void) { return last_error(); }
 
+void mf_struct_sizes(int32_t *options_bytes, int32_t *stats_bytes) {
+  if (options_bytes) *options_bytes = (int32_t)sizeof(mf_options);
+  if (stats_bytes) *stats_bytes = (int32_t)sizeof(mf_stats);
+}
+
 static int create_common(int32_t n, int64_t m, int32_t s, int32_t t, const mf_options *opt, mf_graph **out,
                          mf_graph **gp) {
   clear_error();

@@ -72,7 +72,7 @@ class GraphDesc(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["mf_default_options", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
+EXPORTS = ["mf_default_options", "mf_struct_sizes", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
            "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
            "mf_solve_trace", "mf_destroy_graph", "mf_batch_create", "mf_batch_solve", "mf_batch_get_stats",
            "mf_batch_destroy", "mf_service_create", "mf_submit", "mf_poll", "mf_wait", "mf_service_destroy",
@@ -119,6 +119,13 @@ def lib():
             f.argtypes = [vp, ctypes.POINTER(Options)]
         for f in (L.mf_autotune, L.mf_batch_autotune):
             f.argtypes = [vp, ctypes.POINTER(TuneSpec), ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]
+        L.mf_struct_sizes.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.mf_struct_sizes.restype = None
+        ob, sb = i32(), i32()
+        L.mf_struct_sizes(ctypes.byref(ob), ctypes.byref(sb))
+        if (ob.value, sb.value) != (ctypes.sizeof(Options), ctypes.sizeof(Stats)):
+            raise OSError(f"{LIB_PATH} was built with mf_options/mf_stats of {ob.value}/{sb.value} bytes, the binding "
+                          f"expects {ctypes.sizeof(Options)}/{ctypes.sizeof(Stats)}: rebuild it")
         _lib = L
     return _lib
 

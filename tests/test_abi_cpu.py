@@ -144,3 +144,15 @@ def test_out_of_range_options_rejected_without_gpu(built, field, bad):
     with pytest.raises(mf.MFError) as e:
         mf.Graph(3, np.zeros(4, np.int64), z32, z32, z64, 0, 2, mf.default_options(**{field: bad}))
     assert e.value.code == -1 and field in str(e.value)
+
+
+def test_struct_sizes_match_the_binding(built):
+    import ctypes
+
+    from paper_1507_01926_gb300 import mf
+
+    L = mf.lib()  # also checks the sizes when it loads
+    ob, sb = ctypes.c_int32(), ctypes.c_int32()
+    L.mf_struct_sizes(ctypes.byref(ob), ctypes.byref(sb))
+    assert (ob.value, sb.value) == (ctypes.sizeof(mf.Options), ctypes.sizeof(mf.Stats))
+    L.mf_struct_sizes(None, None)  # both nullable
