@@ -40,6 +40,7 @@ B_VISIT_BFS = 16    # BFS frontier vertex: row offsets 8 + list 8
 B_SLOT_FIXED = 20   # per solve and slot: residual reset (cap 4 + write 4) + flow output (cap 4 + res 4 + out 4)
 B_VERTEX_FIXED = 28  # per solve and vertex: state reset (d 4 + e 8 + addedExcess 8 + stamps 4) + cut 4
 B_VERTEX_GR = 12    # per global relabel and vertex: label reset 4 + rebuild (label 4 + excess ... 4)
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline's denominator)
 
 
 def model_bytes(st: dict, n: int, m: int) -> int:
@@ -562,6 +563,8 @@ def main():
         "scans_per_solve": scans / args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "mf::solve_kernel",
+                     "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": achieved / HBM_NOMINAL_GBS,
+                     "traffic_GBps": (traffic / (statistics.mean(per_step) / 1000.0) / 1e9) if traffic else None,
                      "model_bytes_per_launch": statistics.mean(mb),
                      "phases": phase_rooflines(stats[len(stats) // 2], g.n, peak)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
