@@ -61,6 +61,34 @@ def phase_rooflines(st: dict, n: int, peak: float) -> dict:
     return out
 
 
+def paired_slot_count(tail, head) -> int:
+    """Slots of the paired-slot CSR of an arc list (include/mf.h): self-loops dropped, the k-th arc u -> v
+    shares its slot pair with the k-th arc v -> u, every other arc gets a pair of its own; so an unordered
+    pair {u, v} takes 2 * max(#(u -> v), #(v -> u)) slots."""
+    tail = np.asarray(tail, np.int64)
+    head = np.asarray(head, np.int64)
+    keep = tail != head
+    tail, head = tail[keep], head[keep]
+    lo, hi = np.minimum(tail, head), np.maximum(tail, head)
+    n = int(max(hi.max(), 0)) + 1 if hi.size else 1
+    fwd = tail < head
+    key = lo * n + hi
+    cf = np.unique(key[fwd], return_counts=True)
+    cb = np.unique(key[~fwd], return_counts=True)
+    keys = np.union1d(cf[0], cb[0])
+    a = np.zeros(keys.size, np.int64)
+    b = np.zeros(keys.size, np.int64)
+    a[np.searchsorted(keys, cf[0])] = cf[1]
+    b[np.searchsorted(keys, cb[0])] = cb[1]
+    return int(2 * np.maximum(a, b).sum())
+
+
+def workload_config(g, slots: int, world: int, name: str) -> dict:
+    """The `config` object of a bench line, the same for both arms."""
+    return {"workload": name, "n": g.n, "slots": slots, "arcs": g.m, "global_batch": world,
+            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (about 1.3 GB of device state per solve)"}
+
+
 def apply_overrides(opt, args):
     """Sets the mf_options fields given by --options (a JSON object) on opt."""
     if args.options:
@@ -232,7 +260,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "arcs": g.m},
+            "data": "synthetic", "config": workload_config(g, paired_slot_count(g.tail, g.head), world, WORKLOAD),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -552,10 +580,7 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if tuple(args.grid3d) == (256, 256, 128) else g.name,
-                   "n": g.n, "slots": csr.m, "arcs": g.m, "global_batch": world,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (about 1.3 GB of device state per solve)"},
+        "config": workload_config(g, csr.m, world, WORKLOAD if tuple(args.grid3d) == (256, 256, 128) else g.name),
         "solve_ms": statistics.median(per_step), "solve_ms_all": [round(x, 3) for x in per_step],
         "preflow_ms": statistics.median(s["preflow_ms"] for s in stats),
         "flow_value": flow_value, "flow_value_matches_oracle": (gold == flow_value) if gold is not None else None,

@@ -57,3 +57,24 @@ def test_sized_oracle_sample_stops_near_its_target(built):
     assert limit >= 20_000_000 or not r["truncated"]
     assert r["seconds"] < 5.0  # the geometric growth never overshoots by much
     assert r["stats"]["scans"] > 0
+
+
+@pytest.mark.parametrize("which", ["grid", "random", "rmat", "multi"])
+def test_paired_slot_count_equals_the_builder(built, which):
+    """The reference arm reports the same slot count as the CSR builder without calling the solver library."""
+    import numpy as np
+
+    from paper_1507_01926_gb300 import inputs as I
+    from paper_1507_01926_gb300 import mf
+
+    if which == "multi":  # parallel and antiparallel multi-arcs and self-loops
+        rng = np.random.default_rng(5)
+        tail = rng.integers(0, 12, 300).astype(np.int32)
+        head = rng.integers(0, 12, 300).astype(np.int32)
+        n = 12
+        cap = np.ones(300, np.int32)
+    else:
+        g = {"grid": lambda: I.grid3d(9, 8, 7, 31), "random": lambda: I.random_graph(80, 900, 32),
+             "rmat": lambda: I.rmat(9, 8, 33)}[which]()
+        n, tail, head, cap = g.n, g.tail, g.head, g.cap
+    assert bench.paired_slot_count(tail, head) == mf.build_csr(n, tail, head, cap).m
