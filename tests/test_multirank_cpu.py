@@ -37,7 +37,7 @@ def test_two_rank_aggregation_gloo():
     import torch.multiprocessing as mp
 
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a process that already runs threads
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
