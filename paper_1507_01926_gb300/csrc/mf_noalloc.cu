@@ -1,9 +1,9 @@
 // mf_solve_noalloc: a max-flow solve that allocates nothing.
 //
 // Some callers cannot call cudaMalloc: code running inside another runtime's
-// memory pool or under a strict memory budget, plug-ins that must not touch
-// the CUDA allocator while a CUDA graph is being captured, or services that
-// have pre-committed all device memory at start-up. They hold the graph and
+// memory pool or under a strict memory budget, plug-ins that must leave the
+// CUDA allocator alone, or services that have pre-committed all device memory
+// at start-up. They hold the graph and
 // the outputs in device memory already; what the solve needs beyond that
 // (residuals, labels, excesses, vertex lists, the control block) is placed
 // in one fixed scratch area that the library declares statically, so the call
