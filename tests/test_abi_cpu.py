@@ -156,3 +156,29 @@ def test_struct_sizes_match_the_binding(built):
     L.mf_struct_sizes(ctypes.byref(ob), ctypes.byref(sb))
     assert (ob.value, sb.value) == (ctypes.sizeof(mf.Options), ctypes.sizeof(mf.Stats))
     L.mf_struct_sizes(None, None)  # both nullable
+
+
+def _struct_fields(src, name):
+    """Field names, in order, of `typedef struct name { ... } name;` in the header (comments removed)."""
+    import re
+
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[\d+\]", "", decl)  # arrays: the name is what matters
+        typ, rest = decl.split(None, 1) if " " in decl else (decl, "")
+        names += [x.strip().lstrip("*") for x in rest.split(",")]
+    return names
+
+
+def test_binding_structs_follow_the_header(built):
+    """mf.py's ctypes copies of mf_options and mf_stats have the header's fields in the header's order."""
+    from paper_1507_01926_gb300 import mf
+
+    src = open(os.path.join(ROOT, "include", "mf.h")).read()
+    assert _struct_fields(src, "mf_options") == [f for f, _ in mf.Options._fields_]
+    assert _struct_fields(src, "mf_stats") == [f for f, _ in mf.Stats._fields_]
