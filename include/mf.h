@@ -145,10 +145,18 @@ typedef struct mf_options {
   /* Serving: most requests a lane packs into one persistent launch (0 = as
    * many as are queued and fit the budget, the default). */
   int32_t union_max_requests;
+  /* Batches and service unions: 1 (default) = a global relabel taken while
+   * some vertex is active covers only the instances that hold active vertices
+   * (the others have no excess to move, and no arc joins two instances); the
+   * first relabel of a phase and the one that confirms its end cover every
+   * instance. 0 = every global relabel covers every instance. Same results. */
+  int32_t live_relabel;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
- * discharge pass or a BFS expansion. */
+ * discharge pass (a relabel pass of the simple rounds) or a BFS expansion,
+ * slots with zero residual included; scans_discharge_residual counts the
+ * discharge scans of slots with positive residual. */
 typedef struct mf_stats {
   int64_t rounds;           /* push-relabel rounds, both phases */
   int64_t rounds_phase1;
@@ -171,6 +179,8 @@ typedef struct mf_stats {
   int32_t grid_blocks;      /* persistent-kernel CTAs */
   int32_t block_threads;
   int64_t gap_lifted;       /* vertices lifted to label n by gap relabeling */
+  int64_t scans_discharge_residual;
+  int64_t global_relabels_partial; /* of global_relabels, those that covered only some instances */
 } mf_stats;
 
 typedef struct mf_graph mf_graph;
@@ -372,10 +382,13 @@ void mf_service_destroy(mf_service *svc);
  * that every GPU loading the library holds until the process exits; a graph
  * needing more (about 56 bytes per vertex + 8 per slot) is rejected with
  * MF_ERR_TOO_LARGE before any work. The call allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine. The first call on each device looks
- * up the scratch area's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture. Every call on a device uses the same scratch
- * area and re-initialises it; calls whose work overlaps on the GPU race.
+ * cudaFree or allocating library routine. Every call looks up the scratch
+ * area's device address (cudaGetSymbolAddress). With lazy module loading (the
+ * CUDA default) the first call on a device loads the library's device code
+ * there, and that commits the 32 MiB area: make that first call at start-up,
+ * before the rest of device memory is committed and before any stream capture.
+ * Every call on a device uses the same scratch area and re-initialises it;
+ * calls whose work overlaps on the GPU race.
  */
 int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, const int32_t *d_head, const int32_t *d_cap,
                      const int32_t *d_rev, int32_t s, int32_t t, int64_t *d_value, int32_t *d_flow,

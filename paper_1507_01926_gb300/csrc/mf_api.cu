@@ -129,23 +129,41 @@ static int flags_to_status(unsigned f) {
 
 // ------------------------------------------------------------------ graph
 
+// Device memory of a graph: cudaMalloc, or for a service lane's union the
+// lane's pool in stream order (cudaFree would wait for the other lanes' work).
+int galloc(mf_graph *g, void **p, size_t bytes, const char *what) {
+  if (!bytes) bytes = 16;
+  const cudaError_t e = g->pool ? cudaMallocFromPoolAsync(p, bytes, g->pool, g->stream) : cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
+  return MF_OK;
+}
+
+void gfree(mf_graph *g, void *p) {
+  if (!p) return;
+  if (g->pool)
+    cudaFreeAsync(p, g->stream);
+  else
+    cudaFree(p);
+}
+
 static void free_graph_buffers(mf_graph *g) {
   void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab, g->list[0], g->list[1], g->list[2],
-                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap, g->hist};
-  for (void *p : ps)
-    if (p) cudaFree(p);
+                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap, g->hist,
+                g->tiles, g->voff, g->live, g->cwoff, g->d_cutw};
+  for (void *p : ps) gfree(g, p);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
-  if (g->h_ctl) cudaFreeHost(g->h_ctl);
-  if (g->ev0) cudaEventDestroy(g->ev0);
-  if (g->ev1) cudaEventDestroy(g->ev1);
+  if (!g->lane_host) {
+    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+  }
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
 }
 
-static int dalloc(void **p, size_t bytes, const char *what) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-  if (e != cudaSuccess) return cuda_fail(e, what);
-  return MF_OK;
-}
+static int dalloc(mf_graph *g, void **p, size_t bytes, const char *what) { return galloc(g, p, bytes, what); }
 
 #define TRY(x)               \
   do {                       \
@@ -169,19 +187,20 @@ static int dalloc(void **p, size_t bytes, const char *what) {
 int alloc_state(mf_graph *g) {
   const size_t n = (size_t)g->n, m = (size_t)g->m;
   int rc;
-  if ((rc = dalloc((void **)&g->row, (n + 1) * 4, "cudaMalloc row"))) return rc;
-  if ((rc = dalloc((void **)&g->head, m * 4, "cudaMalloc head"))) return rc;
-  if ((rc = dalloc((void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
-  if ((rc = dalloc((void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
-  if ((rc = dalloc((void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
-  if ((rc = dalloc((void **)&g->vs, n * sizeof(VRec), "cudaMalloc vertex state"))) return rc;
-  if ((rc = dalloc((void **)&g->blab, n * 8, "cudaMalloc BFS labels"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->row, (n + 1) * 4, "cudaMalloc row"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->head, m * 4, "cudaMalloc head"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->rev, m * 4, "cudaMalloc rev"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->cap, m * 4, "cudaMalloc cap"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->rr, m * 8, "cudaMalloc residuals"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->vs, n * sizeof(VRec), "cudaMalloc vertex state"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->blab, n * 8, "cudaMalloc BFS labels"))) return rc;
   for (int k = 0; k < 3; k++)
-    if ((rc = dalloc((void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
-  if ((rc = dalloc((void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
-  if ((rc = dalloc((void **)&g->snk, (size_t)g->ninst * 4, "cudaMalloc sinks"))) return rc;
-  if ((rc = dalloc((void **)&g->ctl, sizeof(Ctl), "cudaMalloc control block"))) return rc;
-  if ((rc = dalloc((void **)&g->d_value, (size_t)g->ninst * 8, "cudaMalloc value"))) return rc;
+    if ((rc = dalloc(g, (void **)&g->list[k], n * 4, "cudaMalloc list"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->src, (size_t)g->ninst * 4, "cudaMalloc sources"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->snk, (size_t)g->ninst * 4, "cudaMalloc sinks"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->ctl, sizeof(Ctl), "cudaMalloc control block"))) return rc;
+  if ((rc = dalloc(g, (void **)&g->d_value, (size_t)g->ninst * 8, "cudaMalloc value"))) return rc;
+  if (g->lane_host) return MF_OK;  // pinned control-block copy and events come from the service lane
   cudaError_t e = cudaMallocHost((void **)&g->h_ctl, sizeof(Ctl));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
   if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -194,8 +213,9 @@ int alloc_state(mf_graph *g) {
 int validate_on_device(mf_graph *g, const long long *row64, const long long *rev64, cudaStream_t st) {
   unsigned *flags = nullptr;
   unsigned long long *marcs = nullptr;
-  cudaError_t e = cudaMalloc((void **)&flags, 16);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc flags");
+  int arc = galloc(g, (void **)&flags, 16, "cudaMalloc flags");
+  if (arc) return arc;
+  cudaError_t e;
   marcs = reinterpret_cast<unsigned long long *>(flags) + 1;
   cudaMemsetAsync(flags, 0, 16, st);
   const int T = 256;
@@ -208,7 +228,7 @@ int validate_on_device(mf_graph *g, const long long *row64, const long long *rev
   e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    cudaFree(flags);
+    gfree(g, flags);
     return cuda_fail(e, "graph validation");
   }
   if (h[0] == 0 && g->m > 0) {
@@ -219,11 +239,11 @@ int validate_on_device(mf_graph *g, const long long *row64, const long long *rev
     e = cudaMemcpyAsync(h, flags, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-      cudaFree(flags);
+      gfree(g, flags);
       return cuda_fail(e, "graph validation");
     }
   }
-  cudaFree(flags);
+  gfree(g, flags);
   g->m_arcs = (long long)((unsigned long long)h[2] | ((unsigned long long)h[3] << 32));
   g->max_degree = h[1];
   return flags_to_status(h[0]);
@@ -258,6 +278,7 @@ int check_options(const mf_options *o) {
   if (o->gap_every < 0) return fail(MF_ERR_INVALID_ARG, "gap_every must be >= 0");
   if (o->bfs_pull < 0) return fail(MF_ERR_INVALID_ARG, "bfs_pull must be >= 0");
   if (o->union_max_requests < 0) return fail(MF_ERR_INVALID_ARG, "union_max_requests must be >= 0");
+  if (o->live_relabel != 0 && o->live_relabel != 1) return fail(MF_ERR_INVALID_ARG, "live_relabel must be 0 or 1");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
@@ -269,6 +290,13 @@ int check_options(const mf_options *o) {
     return fail(MF_ERR_INVALID_ARG, "kernel_variant %d takes bin_thread <= %d", o->kernel_variant,
                 solver_variant_max_bin_thread(o->kernel_variant));
   return MF_OK;
+}
+
+// Relabel work after which a global relabel runs: (alpha n + m) / freq, m
+// counting the slots with positive capacity (Algorithm 1), clamped to int64.
+long long relabel_threshold(const mf_options &o, long long n, long long m_arcs) {
+  const double thr = ((double)o.gr_alpha * (double)n + (double)m_arcs) / o.gr_freq;
+  return thr > 9.0e18 ? (long long)9e18 : (long long)thr;
 }
 
 Dev make_dev(const mf_graph *g) {
@@ -289,12 +317,16 @@ Dev make_dev(const mf_graph *g) {
   D.src = g->src;
   D.snk = g->snk;
   D.ninst = g->ninst;
+  D.tiles = g->tiles;
+  D.ntiles = g->ntiles;
+  D.voff = g->voff;
+  D.live = g->live;
+  D.live_relabel = g->opt.live_relabel;
   D.ctl = g->ctl;
   D.bin_thread = g->opt.bin_thread;
   D.bin_warp = g->opt.bin_warp;
   D.beta = g->opt.work_beta;
-  const double thr = ((double)g->opt.gr_alpha * (double)g->n_total_for_gr + (double)g->m_arcs) / g->opt.gr_freq;
-  D.gr_threshold = thr > 9.0e18 ? (long long)9e18 : (long long)thr;
+  D.gr_threshold = relabel_threshold(g->opt, g->n_total_for_gr, g->m_arcs);
   D.max_rounds = g->opt.max_rounds > 0 ? g->opt.max_rounds : 2000000LL;
   D.simple = g->opt.simple_rounds ? 1 : 0;
   D.cta_vertices = g->max_degree > (long long)g->opt.bin_warp ? 1 : 0;
@@ -404,20 +436,26 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   s.grid_blocks = g->grid;
   s.block_threads = g->block;
   s.gap_lifted = c.gap_lifted;
-  if (c.err) {
-    static const char *where[] = {"init barrier", "saturation barrier", "relabel BFS", "working-set rebuild",
-                                  "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
-                                  "phase-2 excess check", "cut BFS", "round limit", "list capacity",
-                                  "settle barrier", "gap relabeling"};
-    const char *w = (c.err_where >= 0 && c.err_where <= 13) ? where[c.err_where] : "?";
-    if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
-    if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);
-    if (c.err == MF_ERR_INTERNAL && c.err_where == 8)
-      return fail(MF_ERR_INTERNAL, "self-check failed: %lld vertices kept excess", c.leftover);
-    if (c.err == MF_ERR_INTERNAL) return fail(MF_ERR_INTERNAL, "self-check failed (%s)", w);
-    return fail(c.err, "device error %d (%s)", c.err, w);
-  }
-  return MF_OK;
+  s.scans_discharge_residual = c.scans_res;
+  s.global_relabels_partial = c.grs_partial;
+  return device_status(c);
+}
+
+// Status of a finished launch from its control block: MF_OK, or the error the
+// kernel recorded with the site (err_where) that recorded it.
+int device_status(const Ctl &c) {
+  if (!c.err) return MF_OK;
+  static const char *where[] = {"init barrier", "saturation barrier", "relabel BFS", "working-set rebuild",
+                                "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
+                                "phase-2 excess check", "cut BFS", "round limit", "list capacity",
+                                "settle barrier", "gap relabeling"};
+  const char *w = (c.err_where >= 0 && c.err_where <= 13) ? where[c.err_where] : "?";
+  if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
+  if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);
+  if (c.err == MF_ERR_INTERNAL && c.err_where == 8)
+    return fail(MF_ERR_INTERNAL, "self-check failed: %lld vertices kept excess", c.leftover);
+  if (c.err == MF_ERR_INTERNAL) return fail(MF_ERR_INTERNAL, "self-check failed (%s)", w);
+  return fail(c.err, "device error %d (%s)", c.err, w);
 }
 
 }  // namespace mf
@@ -444,6 +482,7 @@ void mf_default_options(mf_options *o) {
   o->local_lists = 1;
   o->bfs_hops = 8;
   o->bfs_pull = 50;
+  o->live_relabel = 1;
 }
 
 const char *mf_last_error(void) { return last_error(); }

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "mf.h"
@@ -20,13 +21,41 @@ struct mf_batch {
   int count = 0;
   std::vector<int> n, s, t;
   std::vector<long long> m, voff, moff;
+  std::vector<long long> cwoff;  // first word of every instance's cut bitmap in g->d_cutw (count + 1)
 };
 
 namespace mf {
 
+// Runs f(k) for every instance k on the host cores: contiguous runs of
+// instances of about equal slot counts (moff = first slot of each instance,
+// M = all slots), one thread per run.
+template <typename F>
+static void parallel_instances(int count, const std::vector<long long> &moff, long long M, F f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = nt == 0 ? 1 : (nt > 64 ? 64 : nt);
+  if (count < 2 * (int)nt || M < (1LL << 20)) nt = 1;
+  if (nt == 1) {
+    for (int k = 0; k < count; k++) f(k);
+    return;
+  }
+  std::vector<std::thread> th;
+  int k0 = 0;
+  for (unsigned j = 0; j < nt && k0 < count; j++) {
+    const long long target = M * (long long)(j + 1) / (long long)nt;
+    int k1 = k0 + 1;
+    while (k1 < count && (j + 1 == nt || moff[(size_t)k1] < target)) k1++;
+    th.emplace_back([=, &f] {
+      for (int k = k0; k < k1; k++) f(k);
+    });
+    k0 = k1;
+  }
+  for (int k = k0; k < count; k++) f(k);
+  for (auto &t : th) t.join();
+}
+
 // Packs `count` host descriptions into one union CSR on the device of opt.
 int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *opt, cudaStream_t stream,
-                 mf_batch *b) {
+                 mf_batch *b, const LaneHost *lane) {
   long long N = 0, M = 0;
   b->count = count;
   for (int k = 0; k < count; k++) {
@@ -48,28 +77,50 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
   }
   if (N > UNV - 4) return fail(MF_ERR_TOO_LARGE, "batch has %lld vertices, beyond the label range", N);
   if (M > 2147483646LL) return fail(MF_ERR_TOO_LARGE, "batch has %lld slots, beyond INT32_MAX", M);
-  // host packing with per-instance range checks (offsets must not leak across instances)
+  // host packing with per-instance range checks (offsets must not leak across instances), spread over the
+  // host cores by instance (each instance writes its own ranges)
   std::vector<long long> row((size_t)N + 1), rev((size_t)(M > 0 ? M : 1));
   std::vector<int> head((size_t)(M > 0 ? M : 1)), cap((size_t)(M > 0 ? M : 1)), ncap((size_t)N), src(count), snk(count);
-  for (int k = 0; k < count; k++) {
+  std::vector<int> bad(count, 0);  // 1: row offsets, 2: not monotone, 3: head, 4: rev
+  std::vector<long long> maxdeg_inst(count, 0);
+  parallel_instances(count, b->moff, M, [&](int k) {
     const mf_graph_desc &d = descs[k];
     const long long V = b->voff[k], S = b->moff[k];
-    if (d.row_offsets[0] != 0 || d.row_offsets[d.n] != d.m)
-      return fail(MF_ERR_INVALID_ARG, "instance %d: row_offsets must run from 0 to m", k);
+    if (d.row_offsets[0] != 0 || d.row_offsets[d.n] != d.m) {
+      bad[k] = 1;
+      return;
+    }
+    long long md = 0;
     for (int v = 0; v < d.n; v++) {
-      if (d.row_offsets[v] > d.row_offsets[v + 1]) return fail(MF_ERR_INVALID_ARG, "instance %d: row_offsets not monotone", k);
+      if (d.row_offsets[v] > d.row_offsets[v + 1]) {
+        bad[k] = 2;
+        return;
+      }
       row[(size_t)(V + v)] = S + d.row_offsets[v];
       ncap[(size_t)(V + v)] = d.n;
+      if (v != d.s && v != d.t) md = std::max(md, (long long)(d.row_offsets[v + 1] - d.row_offsets[v]));
     }
     for (long long a = 0; a < d.m; a++) {
-      if (d.head[a] < 0 || d.head[a] >= d.n) return fail(MF_ERR_INVALID_ARG, "instance %d: head out of range", k);
-      if (d.rev[a] < 0 || d.rev[a] >= d.m) return fail(MF_ERR_INVALID_ARG, "instance %d: rev out of range", k);
+      if (d.head[a] < 0 || d.head[a] >= d.n) {
+        bad[k] = 3;
+        return;
+      }
+      if (d.rev[a] < 0 || d.rev[a] >= d.m) {
+        bad[k] = 4;
+        return;
+      }
       head[(size_t)(S + a)] = (int)(V + d.head[a]);
       rev[(size_t)(S + a)] = S + d.rev[a];
       cap[(size_t)(S + a)] = d.cap[a];
     }
     src[k] = (int)(V + d.s);
     snk[k] = (int)(V + d.t);
+    maxdeg_inst[k] = md;
+  });
+  for (int k = 0; k < count; k++) {
+    static const char *what[] = {"", "row_offsets must run from 0 to m", "row_offsets not monotone",
+                                 "head out of range", "rev out of range"};
+    if (bad[k]) return fail(MF_ERR_INVALID_ARG, "instance %d: %s", k, what[bad[k]]);
   }
   row[(size_t)N] = M;
 
@@ -101,13 +152,37 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
       return cuda_fail(e, "cudaStreamCreate");
     g->own_stream = true;
   }
+  if (lane) {
+    g->pool = lane->pool;
+    g->lane_host = true;
+    g->h_ctl = lane->h_ctl;
+    g->ev0 = lane->ev0;
+    g->ev1 = lane->ev1;
+  }
   if ((rc = alloc_state(g))) return rc;
-  if ((e = cudaMalloc((void **)&g->ncap, (size_t)N * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc label caps");
+  if ((rc = galloc(g, (void **)&g->ncap, (size_t)N * 4, "cudaMalloc label caps"))) return rc;
+  // instance vertex offsets and tiles (runs of at most TILE_VERTICES vertices of one instance) for the
+  // global relabels that cover only some instances
+  std::vector<int> voff((size_t)count + 1);
+  std::vector<int4> tiles;
+  for (int k = 0; k < count; k++) {
+    const int V = (int)b->voff[(size_t)k], nk = descs[k].n;
+    voff[(size_t)k] = V;
+    for (int a = 0; a < nk; a += TILE_VERTICES) tiles.push_back(make_int4(V + a, V + std::min(nk, a + TILE_VERTICES), k, 0));
+  }
+  voff[(size_t)count] = (int)N;
+  g->ntiles = (int)tiles.size();
+  b->cwoff.assign((size_t)count + 1, 0);
+  for (int k = 0; k < count; k++) b->cwoff[(size_t)k + 1] = b->cwoff[(size_t)k] + (descs[k].n + 31) / 32;
+  if ((rc = galloc(g, (void **)&g->voff, voff.size() * 4, "cudaMalloc instance offsets"))) return rc;
+  if ((rc = galloc(g, (void **)&g->tiles, tiles.size() * sizeof(int4), "cudaMalloc tiles"))) return rc;
+  if ((rc = galloc(g, (void **)&g->live, (size_t)count * 4, "cudaMalloc instance flags"))) return rc;
+  if ((rc = galloc(g, (void **)&g->cwoff, b->cwoff.size() * 8, "cudaMalloc cut offsets"))) return rc;
   long long *row64 = nullptr, *rev64 = nullptr;
-  if ((e = cudaMalloc((void **)&row64, ((size_t)N + 1) * 8)) != cudaSuccess) return cuda_fail(e, "cudaMalloc staging");
-  if ((e = cudaMalloc((void **)&rev64, (size_t)(M > 0 ? M : 1) * 8)) != cudaSuccess) {
-    cudaFree(row64);
-    return cuda_fail(e, "cudaMalloc staging");
+  if ((rc = galloc(g, (void **)&row64, ((size_t)N + 1) * 8, "cudaMalloc staging"))) return rc;
+  if ((rc = galloc(g, (void **)&rev64, (size_t)(M > 0 ? M : 1) * 8, "cudaMalloc staging"))) {
+    gfree(g, row64);
+    return rc;
   }
   e = cudaMemcpyAsync(row64, row.data(), ((size_t)N + 1) * 8, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(rev64, rev.data(), (size_t)M * 8, cudaMemcpyHostToDevice, g->stream);
@@ -116,27 +191,55 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->ncap, ncap.data(), (size_t)N * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->src, src.data(), (size_t)count * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->snk, snk.data(), (size_t)count * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->voff, voff.data(), voff.size() * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->cwoff, b->cwoff.data(), b->cwoff.size() * 8, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);  // host vectors go out of scope below
   if (e != cudaSuccess) {
-    cudaFree(row64);
-    cudaFree(rev64);
+    gfree(g, row64);
+    gfree(g, rev64);
     return cuda_fail(e, "host-to-device copy");
   }
   rc = validate_on_device(g, row64, rev64, g->stream);
-  cudaFree(row64);
-  cudaFree(rev64);
+  gfree(g, row64);
+  gfree(g, rev64);
   if (rc) return rc;
   long long maxdeg = 0;  // over all instances, sources and sinks excluded
-  for (int k = 0; k < count; k++) {
-    const mf_graph_desc &d = descs[k];
-    for (int v = 0; v < d.n; v++)
-      if (v != d.s && v != d.t) maxdeg = std::max(maxdeg, (long long)(d.row_offsets[v + 1] - d.row_offsets[v]));
-  }
+  for (int k = 0; k < count; k++) maxdeg = std::max(maxdeg, maxdeg_inst[(size_t)k]);
   g->max_degree = maxdeg;
   return launch_config(g);
 }
 
-// Solves the packed union and splits the outputs per instance (host arrays).
+// Copies each instance's part of the union's cut bitmap (bit u of word u / 32)
+// to its own run of words starting at word cwoff[k] of `out`, bit v of
+// instance k at bit v of its run (words past the instance's n_k bits zero).
+__global__ void k_split_cut(const unsigned *cut, long long words, const int *voff, const long long *cwoff, int count,
+                            unsigned *out) {
+  const long long total = cwoff[count];
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = count;  // cwoff[lo] <= w < cwoff[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (cwoff[mid] <= w) lo = mid; else hi = mid;
+    }
+    const long long j = w - cwoff[lo];
+    const long long left = (long long)(voff[lo + 1] - voff[lo]) - 32 * j;  // >= 1
+    const long long u = (long long)voff[lo] + 32 * j;                       // union bit of the word's first bit
+    const long long q = u >> 5;
+    const int r = (int)(u & 31);
+    unsigned x = cut[q] >> r;
+    if (r && q + 1 < words) x |= cut[q + 1] << (32 - r);
+    if (left < 32) x &= (1u << left) - 1u;
+    out[w] = x;
+  }
+}
+
+// Solves the packed union and copies the outputs of every instance to its host
+// arrays: values, the instance's slice of the per-slot flow, and its cut
+// bitmap (split on the device).
 int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits) {
   mf_graph *g = b->g;
   bool want_flow = false, want_cut = false;
@@ -147,46 +250,43 @@ int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cu
   if (g->opt.cut_only && want_flow) return fail(MF_ERR_INVALID_ARG, "cut_only solves produce no per-arc flow");
   cudaError_t e = cudaSetDevice(g->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  if (want_flow && !g->d_flow && (e = cudaMalloc((void **)&g->d_flow, (size_t)(g->m > 0 ? g->m : 1) * 4)) != cudaSuccess)
-    return cuda_fail(e, "cudaMalloc flow output");
+  int rc;
+  if (want_flow && !g->d_flow && (rc = galloc(g, (void **)&g->d_flow, (size_t)g->m * 4, "cudaMalloc flow output")))
+    return rc;
   const size_t words = ((size_t)g->n + 31) / 32;
-  if (want_cut && !g->d_cut && (e = cudaMalloc((void **)&g->d_cut, words * 4)) != cudaSuccess)
-    return cuda_fail(e, "cudaMalloc cut output");
+  if (want_cut && !g->d_cut && (rc = galloc(g, (void **)&g->d_cut, words * 4, "cudaMalloc cut output"))) return rc;
+  if (want_cut && !g->d_cutw &&
+      (rc = galloc(g, (void **)&g->d_cutw, (size_t)b->cwoff[(size_t)b->count] * 4, "cudaMalloc cut outputs")))
+    return rc;
   Dev D = make_dev(g);
   D.out_value = g->d_value;
   D.out_flow = want_flow ? g->d_flow : nullptr;
   D.out_cut = want_cut ? g->d_cut : nullptr;
-  int rc = run_kernel(g, D, g->stream);
+  rc = run_kernel(g, D, g->stream);
   if (rc) return rc;
+  if (want_cut) {
+    const long long total = b->cwoff[(size_t)b->count];
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    k_split_cut<<<blocks > 0 ? blocks : 1, 256, 0, g->stream>>>(g->d_cut, (long long)words, g->voff, g->cwoff,
+                                                              b->count, g->d_cutw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cut split");
+  }
   std::vector<long long> vals((size_t)b->count);
   e = cudaMemcpyAsync(vals.data(), g->d_value, (size_t)b->count * 8, cudaMemcpyDeviceToHost, g->stream);
-  std::vector<int> flow;
-  std::vector<unsigned> cut;
-  if (e == cudaSuccess && want_flow) {
-    flow.resize((size_t)g->m);
-    e = cudaMemcpyAsync(flow.data(), g->d_flow, (size_t)g->m * 4, cudaMemcpyDeviceToHost, g->stream);
-  }
-  if (e == cudaSuccess && want_cut) {
-    cut.resize(words);
-    e = cudaMemcpyAsync(cut.data(), g->d_cut, words * 4, cudaMemcpyDeviceToHost, g->stream);
+  for (int k = 0; k < b->count && e == cudaSuccess; k++) {
+    if (want_flow && arc_flows[k] && b->m[(size_t)k] > 0)
+      e = cudaMemcpyAsync(arc_flows[k], g->d_flow + b->moff[(size_t)k], (size_t)b->m[(size_t)k] * 4,
+                          cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && want_cut && cut_bits[k])
+      e = cudaMemcpyAsync(cut_bits[k], g->d_cutw + b->cwoff[(size_t)k],
+                          (size_t)(b->cwoff[(size_t)k + 1] - b->cwoff[(size_t)k]) * 4, cudaMemcpyDeviceToHost,
+                          g->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of the outputs");
-  for (int k = 0; k < b->count; k++) {
-    if (values) values[k] = vals[(size_t)k];
-    if (want_flow && arc_flows[k] && b->m[(size_t)k] > 0)
-      memcpy(arc_flows[k], flow.data() + b->moff[(size_t)k], (size_t)b->m[(size_t)k] * 4);
-    if (want_cut && cut_bits[k]) {
-      const long long V = b->voff[(size_t)k];
-      const int nk = b->n[(size_t)k];
-      uint32_t *out = cut_bits[k];
-      memset(out, 0, ((size_t)nk + 31) / 32 * 4);
-      for (int v = 0; v < nk; v++) {
-        const long long u = V + v;
-        if ((cut[(size_t)(u >> 5)] >> (u & 31)) & 1u) out[v >> 5] |= 1u << (v & 31);
-      }
-    }
-  }
+  if (values)
+    for (int k = 0; k < b->count; k++) values[k] = vals[(size_t)k];
   return MF_OK;
 }
 
@@ -208,7 +308,7 @@ int mf_batch_create(int32_t count, const mf_graph_desc *descs, const mf_options 
   *out = nullptr;
   if (count < 1 || !descs) return fail(MF_ERR_INVALID_ARG, "count must be >= 1 with descriptions");
   mf_batch *b = new mf_batch();
-  int rc = create_union(count, descs, opt, nullptr, b);
+  int rc = create_union(count, descs, opt, nullptr, b, nullptr);
   if (rc) {
     destroy_union(b);
     return rc;

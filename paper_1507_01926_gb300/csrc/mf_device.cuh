@@ -6,6 +6,9 @@
 
 namespace mf {
 
+// Vertices per tile of a multi-instance graph (Dev::tiles).
+constexpr int TILE_VERTICES = 4096;
+
 // Sentinel label of a vertex not yet reached by a BFS; a source-role vertex
 // carries UNV + 1 during a BFS so that it is never discovered.
 constexpr int UNV = 0x3fffffff;
@@ -39,6 +42,8 @@ struct Ctl {
   int stopped_round;   // MODE_ROUNDS: rounds run
   int gap;             // gap relabeling: smallest label without a vertex (INT_MAX: none found yet)
   long long gap_lifted;  // vertices lifted to the label cap by gap relabeling
+  long long scans_res;   // discharge scans of slots with positive residual
+  long long grs_partial;  // global relabels that covered only the live instances
 };
 // the kernel reads cnt as one int4 and gr_req as one int2
 static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, lcnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0,
@@ -84,6 +89,15 @@ struct Dev {
   const int *src;    // sources (phase 1), one per instance
   const int *snk;    // sinks (phase 1), one per instance
   int ninst;
+  // multi-instance graphs (nullptr otherwise): runs of at most TILE_VERTICES
+  // vertices of one instance {first vertex, end, instance, 0}, the first vertex
+  // of every instance (ninst + 1 entries), and per instance the number of the
+  // last partial global relabel that covers it
+  const int4 *tiles;
+  int ntiles;
+  const int *voff;
+  int *live;
+  int live_relabel;  // 1: a global relabel taken while vertices are active covers only their instances
   Ctl *ctl;
   // options
   int bin_thread;

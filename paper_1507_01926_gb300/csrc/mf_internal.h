@@ -26,6 +26,12 @@ struct mf_graph {
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
   int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)
+  long long *cwoff = nullptr;  // multi-instance graphs: first word of every instance's cut bitmap, ninst + 1
+  unsigned *d_cutw = nullptr;  // multi-instance graphs: the instances' cut bitmaps, each from a word boundary
+  int4 *tiles = nullptr;       // multi-instance graphs: vertex runs of one instance (mf::Dev::tiles)
+  int ntiles = 0;
+  int *voff = nullptr;         // multi-instance graphs: first vertex of every instance, ninst + 1 entries
+  int *live = nullptr;         // multi-instance graphs: per-instance relabel flags
   int *hist = nullptr;         // label counts for gap relabeling (allocated on first use)
   mf::Ctl *ctl = nullptr;
   long long *d_value = nullptr;
@@ -34,6 +40,10 @@ struct mf_graph {
   mf::Ctl *h_ctl = nullptr;    // pinned
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // service lanes: device memory comes from this pool, allocated and freed in stream order on `stream`
+  // (no device-wide synchronisation), and h_ctl / ev0 / ev1 belong to the lane
+  cudaMemPool_t pool = nullptr;
+  bool lane_host = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // captured launch sequence (mf_options.use_graph) and what it was captured for
   cudaGraphExec_t gexec = nullptr;
@@ -43,14 +53,26 @@ struct mf_graph {
 };
 
 namespace mf {
+// What a service lane lends to every union it solves: its memory pool and its
+// pinned control-block copy and timing events.
+struct LaneHost {
+  cudaMemPool_t pool;
+  Ctl *h_ctl;
+  cudaEvent_t ev0, ev1;
+};
+
 int fail(int code, const char *fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char *what);
 int alloc_state(mf_graph *g);
+int galloc(mf_graph *g, void **p, size_t bytes, const char *what);
+void gfree(mf_graph *g, void *p);
 int validate_on_device(mf_graph *g, const long long *row64, const long long *rev64, cudaStream_t st);
 int launch_config(mf_graph *g);
 int check_options(const mf_options *o);
 Dev make_dev(const mf_graph *g);
+long long relabel_threshold(const mf_options &o, long long n, long long m_arcs);
+int device_status(const Ctl &c);
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
 int keep_local_limit(const mf_options &o, long long max_degree, int block_threads);
 int solver_variants();

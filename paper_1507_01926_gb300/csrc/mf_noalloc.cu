@@ -17,8 +17,6 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "mf.h"
 #include "mf_internal.h"
 
@@ -29,10 +27,6 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_scratch_mu;
-unsigned char *g_scratch_addr[MAX_DEVICES];  // device address of the scratch array, per device ordinal
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -66,21 +60,15 @@ Layout layout(long long n, long long m) {
   return L;
 }
 
-// The scratch array's device address on the current device, looked up once
-// per device (cudaGetSymbolAddress, with that device current).
+// The scratch array's device address on the current device. Looked up on
+// every call (no allocation once the module is loaded, and cheap): an address
+// kept from an earlier call would be stale after cudaDeviceReset or a new
+// primary context, which load the module, and the array with it, anew.
 int scratch_base(unsigned char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= MAX_DEVICES) return fail(MF_ERR_CUDA, "device ordinal %d beyond %d", dev, MAX_DEVICES);
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch area");
-    g_scratch_addr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_scratch_addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch area");
+  *out = static_cast<unsigned char *>(p);
   return MF_OK;
 }
 
@@ -219,7 +207,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.bin_thread = o.bin_thread;
   D.bin_warp = o.bin_warp;
   D.beta = o.work_beta;
-  D.gr_threshold = (long long)(((double)o.gr_alpha * n + (double)marcs) / o.gr_freq);
+  D.gr_threshold = relabel_threshold(o, n, (long long)marcs);
   D.gr_time_ratio = o.gr_time_ratio;
   D.max_rounds = 2000000LL;
   D.timeout_ns = (unsigned long long)o.timeout_ms * 1000000ULL;
@@ -239,8 +227,5 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   e = cudaMemcpyAsync(&c, D.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "solver");
-  if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out");
-  if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached");
-  if (c.err) return fail(c.err, "device error %d", c.err);
-  return MF_OK;
+  return device_status(c);
 }

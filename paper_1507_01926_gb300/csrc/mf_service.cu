@@ -58,6 +58,7 @@ struct mf_service {
   int lanes = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
+  cudaMemPool_t pool = nullptr;  // device memory of the lanes' unions (stream-ordered)
   std::deque<Request *> pending;
   std::unordered_map<mf_ticket, Request *> tickets;
   size_t in_use = 0;
@@ -69,7 +70,7 @@ struct mf_service {
 
 namespace mf {
 int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *opt, cudaStream_t stream,
-                 mf_batch *b);
+                 mf_batch *b, const LaneHost *lane);
 int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits);
 mf_batch *new_batch();
 void destroy_union(mf_batch *b);
@@ -81,6 +82,10 @@ static void lane_main(mf_service *svc, int lane) {
   cudaSetDevice(o.device);
   cudaStream_t stream = nullptr;
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  LaneHost lh{svc->pool, nullptr, nullptr, nullptr};
+  cudaMallocHost((void **)&lh.h_ctl, sizeof(Ctl));
+  cudaEventCreate(&lh.ev0);
+  cudaEventCreate(&lh.ev1);
   for (;;) {
     std::vector<Request *> batch;
     size_t bytes = 0;
@@ -112,8 +117,8 @@ static void lane_main(mf_service *svc, int lane) {
     for (size_t i = 0; i < batch.size(); i++) {
       Request *r = batch[i];
       descs[i] = mf_graph_desc{r->n, r->m, r->row.data(), r->head.data(), r->cap.data(), r->rev.data(), r->s, r->t};
-      r->flow.assign((size_t)r->m, 0);
-      r->cut.assign(((size_t)r->n + 31) / 32, 0);
+      r->flow.resize((size_t)r->m);
+      r->cut.resize(((size_t)r->n + 31) / 32);
     }
     std::vector<int64_t> values(batch.size(), 0);
     std::vector<int32_t *> fl(batch.size());
@@ -123,7 +128,8 @@ static void lane_main(mf_service *svc, int lane) {
       cu[i] = batch[i]->cut.data();
     }
     mf_batch *b = new_batch();
-    int rc = create_union((int32_t)batch.size(), descs.data(), &o, stream, b);
+    int rc = (lh.h_ctl && lh.ev0 && lh.ev1) ? create_union((int32_t)batch.size(), descs.data(), &o, stream, b, &lh)
+                                            : fail(MF_ERR_CUDA, "service lane set-up failed");
     if (rc == MF_OK) rc = solve_union(b, values.data(), fl.data(), cu.data());
     std::string err = rc ? std::string(last_error()) : std::string();
     destroy_union(b);
@@ -153,6 +159,10 @@ static void lane_main(mf_service *svc, int lane) {
     svc->cv_done.notify_all();
     svc->cv_work.notify_all();
   }
+  if (stream) cudaStreamSynchronize(stream);
+  if (lh.h_ctl) cudaFreeHost(lh.h_ctl);
+  if (lh.ev0) cudaEventDestroy(lh.ev0);
+  if (lh.ev1) cudaEventDestroy(lh.ev1);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -177,6 +187,19 @@ int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_serv
     return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", o.block_threads);
   mf_service *svc = new mf_service();
   svc->budget = device_budget_bytes;
+  // one stream-ordered pool for the lanes' unions: freeing a finished union does not wait for the other
+  // lanes' kernels (cudaFree would), and freed memory stays in the pool for the next union
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = o.device;
+  if ((e = cudaMemPoolCreate(&svc->pool, &props)) != cudaSuccess) {
+    delete svc;
+    return cuda_fail(e, "cudaMemPoolCreate");
+  }
+  unsigned long long keep = ~0ULL;
+  cudaMemPoolSetAttribute(svc->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   // one lane per CTA slot of an SM (at most 8): a lane's launch takes one CTA per SM, so the lanes'
   // persistent kernels are resident together and the requests of different lanes overlap on the device
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
@@ -268,6 +291,7 @@ void mf_service_destroy(mf_service *svc) {
   svc->cv_work.notify_all();
   for (auto &t : svc->workers) t.join();
   for (auto &kv : svc->tickets) delete kv.second;
+  if (svc->pool) cudaMemPoolDestroy(svc->pool);
   delete svc;
 }
 

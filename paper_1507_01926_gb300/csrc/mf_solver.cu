@@ -464,9 +464,74 @@ __device__ __forceinline__ int sweep_item(const Sweep &w, int it, int &v) {
   return 0;
 }
 
+// Per-thread counters. scans_dis counts every slot a discharge pass (or a
+// relabel pass of the simple rounds) examines, zero residuals included;
+// scans_res those of them with positive residual.
 struct TStat {
-  long long scans_dis = 0, scans_bfs = 0, pushes = 0, relabels = 0, visits_dis = 0, visits_bfs = 0;
+  long long scans_dis = 0, scans_res = 0, scans_bfs = 0, pushes = 0, relabels = 0, visits_dis = 0, visits_bfs = 0;
 };
+
+// ------------------------------------------------------------------ partial relabels
+//
+// A multi-instance graph (batch or service union) shares rounds and global
+// relabels among its instances. Vertices, labels and arcs of one instance never
+// touch another's, and an instance without an active vertex has no excess to
+// move: a global relabel leaves it as it is. So a relabel taken while some
+// vertex is active covers only the instances of the working set ("live"
+// instances, flagged with the relabel's number `epoch` in D.live); the first
+// relabel of a phase and the one that confirms the end of a phase cover every
+// instance. The vertex loops of such a relabel walk the static tiles of the
+// live instances (D.tiles: runs of vertices of one instance).
+
+struct Sel {
+  bool on;    // cover only the instances whose D.live entry equals epoch
+  int epoch;
+};
+
+// Runs f(v, valid) for every vertex the relabel covers, in sweeps that are
+// uniform across the CTA (valid = false on the lanes past the end of a run,
+// so warp collectives inside f see every lane).
+template <typename F>
+__device__ __forceinline__ void for_covered(const Dev &D, const Sel &S, F f) {
+  if (!S.on) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < D.n; b += stride) {
+      const long long v = b + threadIdx.x;
+      f(v < D.n ? (int)v : 0, v < D.n);
+    }
+    return;
+  }
+  for (int k = blockIdx.x; k < D.ntiles; k += gridDim.x) {
+    const int4 T = __ldg(&D.tiles[k]);
+    if (__ldcg(&D.live[T.z]) != S.epoch) continue;  // uniform in the CTA
+    for (int b = T.x; b < T.y; b += blockDim.x) {
+      const int v = b + (int)threadIdx.x;
+      f(v < T.y ? v : T.x, v < T.y);
+    }
+  }
+}
+
+// Instance of vertex v (binary search over the instance vertex offsets).
+__device__ __forceinline__ int instance_of(const Dev &D, int v) {
+  int lo = 0, hi = D.ninst;  // voff[lo] <= v < voff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&D.voff[mid]) <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Flags the instances of the working set (list generation gen: its global
+// entries and every CTA's kept entries) with `epoch`; ends with a grid barrier.
+__device__ bool mark_live(const Dev &D, Shared &sh, int gen, int epoch) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int cnt = list_count(D, sh, gen);
+  const int *L = list_of(D, gen);
+  for (int i = tid; i < cnt; i += nthr) D.live[instance_of(D, __ldcg(&L[i]))] = epoch;
+  const int *lq = sh.lq[gen % 3];
+  for (int i = threadIdx.x; i < sh.lqn[gen % 3]; i += blockDim.x) D.live[instance_of(D, lq[i])] = epoch;
+  return grid_sync(D, sh, 2);
+}
 
 // ------------------------------------------------------------------ discharge
 //
@@ -600,8 +665,9 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
     bool skipped = false;
 #pragma unroll
     for (int i = 0; i < KTD; i++) {
+      if (i < deg && ex > 0) st.scans_dis++;
       if (i < deg && ex > 0 && rs[i] > 0) {
-        st.scans_dis++;
+        st.scans_res++;
         const bool adm = (dp == dw[i] + 1);
         if (adm && !D.simple && ((act >> i) & 1u) && !wins(dv, dw[i], v, wv[i])) {
           skipped = true;
@@ -682,7 +748,8 @@ __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int 
       const long long total = __shfl_sync(FULL, incl, 31);
       long long delta = 0;
       if (pushable && excl < ex) delta = min((long long)rs, ex - excl);
-      st.scans_dis += (resid ? 1 : 0);
+      st.scans_dis += (i < deg ? 1 : 0);
+      st.scans_res += (resid ? 1 : 0);
       bool found = false;
       if (delta > 0) {
         push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
@@ -768,7 +835,8 @@ __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, 
       const long long excl = wbase + incl_w - pr;
       long long delta = 0;
       if (pushable && excl < ex) delta = min((long long)rs, ex - excl);
-      st.scans_dis += (resid ? 1 : 0);
+      st.scans_dis += (i < deg ? 1 : 0);
+      st.scans_res += (resid ? 1 : 0);
       bool found = false;
       if (delta > 0) {
         push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
@@ -957,8 +1025,13 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int bv = sh.imin[0];
       const int b = __ldg(&D.row[bv]), e = __ldg(&D.row[bv + 1]);
       int m = INT_MAX;
-      for (int a = b + threadIdx.x; a < e; a += blockDim.x)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+      for (int a = b + threadIdx.x; a < e; a += blockDim.x) {
+        st.scans_dis++;
+        if (__ldcg(&D.rr[a]).x > 0) {
+          st.scans_res++;
+          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+        }
+      }
       m = warp_min(m);
       __syncthreads();
       if (lane == 0) sh.imin[wid] = m;
@@ -974,8 +1047,13 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       const int pv = __shfl_sync(FULL, v, leader);
       const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
       int m = INT_MAX;
-      for (int a = b + lane; a < e; a += 32)
-        if (__ldcg(&D.rr[a]).x > 0) m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+      for (int a = b + lane; a < e; a += 32) {
+        st.scans_dis++;
+        if (__ldcg(&D.rr[a]).x > 0) {
+          st.scans_res++;
+          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+        }
+      }
       m = warp_min(m);
       if (lane == leader) {
         cls = 0;
@@ -983,8 +1061,13 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       }
     }
     if (cls == 1) {
-      for (int a = beg; a < beg + deg; a++)
-        if (__ldcg(&D.rr[a]).x > 0) newl = min(newl, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+      for (int a = beg; a < beg + deg; a++) {
+        st.scans_dis++;
+        if (__ldcg(&D.rr[a]).x > 0) {
+          st.scans_res++;
+          newl = min(newl, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+        }
+      }
     }
     if (v >= 0) {
       newl = min(newl, cap_v);
@@ -1185,17 +1268,16 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
 // such an arc exists. Slot a of w's row is (w -> v); the reverse BFS (global
 // relabel) needs c_f(w, v) = res[a], the forward BFS (cut) c_f(v, w) =
 // res[rev[a]]. Thread per vertex up to 32 slots, warp per vertex above.
-__device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int depth, bool reverse, TStat &st) {
+__device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int depth, bool reverse, TStat &st,
+                               const Sel &S) {
   const int next = gen + 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.ctl->cnt[(gen + 2) & 3] = 0;
     D.ctl->lcnt[(gen + 2) & 3] = 0;
   }
   const int lane = threadIdx.x & 31;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < D.n; base += stride) {
-    const long long wl = base + threadIdx.x;
-    const int w = wl < D.n ? (int)wl : -1;
+  for_covered(D, S, [&](int wv, bool valid) {
+    const int w = valid ? wv : -1;
     int beg = 0, deg = 0;
     bool open = false;
     if (w >= 0) {
@@ -1252,7 +1334,7 @@ __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int depth, boo
       }
       __syncwarp();
     }
-  }
+  });
   phase_end(D, sh, next, 0, nullptr);
 }
 
@@ -1260,9 +1342,11 @@ __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int depth, boo
 // `excess_seeds`, every vertex holding excess whose label lies in [1, cap] is
 // a seed as well (cut from the maximum preflow). Returns false on error. On
 // return the last list generation (gen) is empty and no vertex is queued.
+// With S.on only the live instances take part (seeds, blockers and labels of
+// the others are left as they are; no arc leads into them).
 template <int KTD>
 __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *blockers, int nterm, bool reverse,
-                    bool excess_seeds, int &gen, TStat &st, int where) {
+                    bool excess_seeds, int &gen, TStat &st, int where, const Sel &S = Sel{false, 0}) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   const int next = gen + 1;
   // phase A: every label to UNV (excess-holding non-terminals become seeds)
@@ -1270,7 +1354,8 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     D.ctl->cnt[(gen + 2) & 3] = 0;
     D.ctl->lcnt[(gen + 2) & 3] = 0;
   }
-  for (int v = tid; v < D.n; v += nthr) {
+  for_covered(D, S, [&](int v, bool valid) {
+    if (!valid) return;
     unsigned long long x = bword(UNV, 0);
     if (excess_seeds) {
       const int d = __ldcg(lab_ptr(D, v, 0));
@@ -1280,16 +1365,18 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
       }
     }
     D.blab[v] = x;
-  }
+  });
   phase_end(D, sh, next, 0, nullptr);
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   for (int i = tid; i < nterm; i += nthr) {
+    if (S.on && __ldcg(&D.live[i]) != S.epoch) continue;
     D.blab[seeds[i]] = bword(0, BQ);
     if (blockers) D.blab[blockers[i]] = bword(0, BB);
   }
   if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < nterm; i += blockDim.x) append(D, next, seeds[i]);
+    for (int i = threadIdx.x; i < nterm; i += blockDim.x)
+      if (!S.on || __ldcg(&D.live[i]) == S.epoch) append(D, next, seeds[i]);
   if (!grid_sync(D, sh, where)) return false;
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1304,7 +1391,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     // bottom-up when the frontier holds more than n / bfs_pull vertices (only for level-synchronous
     // BFS, where every frontier vertex carries the label `depth`)
     if (D.bfs_pull > 0 && D.bfs_hops == 1 && fcount * D.bfs_pull > D.n)
-      bfs_pull_level(D, sh, gen, depth, reverse, st);
+      bfs_pull_level(D, sh, gen, depth, reverse, st, S);
     else
       bfs_level<KTD>(D, sh, gen, reverse, st);
     const unsigned long long t1 = timer ? gtimer() : 0;
@@ -1334,9 +1421,8 @@ __device__ __forceinline__ int bfs_label(unsigned long long x, int cap) {
 // active. Result: list generation gen.
 template <int KTD>
 __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const int *sources, int r, int &gen,
-                               TStat &st) {
-  if (!bfs<KTD>(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2)) return false;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+                               TStat &st, const Sel &S) {
+  if (!bfs<KTD>(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2, S)) return false;
   const int next = gen + 1;
   const int p = r & 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1344,7 +1430,8 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
     D.ctl->lcnt[(gen + 2) & 3] = 0;
     D.ctl->grs++;
   }
-  for (int v = tid; v < D.n; v += nthr) {
+  for_covered(D, S, [&](int v, bool valid) {
+    if (!valid) return;
     const int c = cap_of(D, v);
     const int d = bfs_label(__ldcg(D.blab + v), c);
     *lab_ptr(D, v, 0) = d;
@@ -1361,7 +1448,7 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
       *act_ptr(D, v, p) = r;
       qpush(D, sh, next, v);
     }
-  }
+  });
   phase_end(D, sh, next, 0, nullptr);
   if (!grid_sync(D, sh, 3, PF_ROUND, next)) return false;
   gen++;
@@ -1428,9 +1515,11 @@ __device__ bool settle(const Dev &D, Shared &sh, int p) {
 // global relabel (or, in MODE_ROUNDS, until stop_rounds rounds ran).
 template <int KTD>
 __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int *sources, int &r, int &gen,
-                          long long &rnd, bool phase1, TStat &st) {
+                          long long &rnd, bool phase1, TStat &st, int &epoch) {
   long long since_gr = LLONG_MAX;
   bool fresh = false, time_req = false, prev_valid = false;
+  bool full_next = true;   // the next global relabel covers every instance (phase start, or an empty working set)
+  bool last_full = false;  // the last global relabel covered every instance
   long long rounds = 0;
   unsigned long long last_gr_ns = 0, last_gr_end = 0;  // meaningful in CTA 0 thread 0 only
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1438,7 +1527,15 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     if (since_gr > D.gr_threshold || time_req) {
       r++;  // fresh stamp: marks of the discarded working set are stale
       const unsigned long long t0 = timer ? gtimer() : 0;
-      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st)) return false;
+      Sel S{D.tiles != nullptr && D.live_relabel != 0 && !full_next, 0};
+      if (S.on) {
+        S.epoch = ++epoch;
+        if (timer) D.ctl->grs_partial++;
+        if (!mark_live(D, sh, gen, S.epoch)) return false;
+      }
+      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st, S)) return false;
+      last_full = !S.on;
+      full_next = false;
       if (timer) {
         last_gr_end = gtimer();
         last_gr_ns = last_gr_end - t0;
@@ -1451,8 +1548,9 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     }
     const long long count = gen_total(D, sh, gen);
     if (count == 0) {
-      if (fresh) break;
-      since_gr = LLONG_MAX;
+      if (fresh && last_full) break;
+      since_gr = LLONG_MAX;  // confirm with a relabel of every instance
+      full_next = true;
       continue;
     }
     if (D.mode == MODE_ROUNDS && rounds >= D.stop_rounds) break;
@@ -1498,7 +1596,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
     if (timer) D.ctl->stopped_round = (int)rounds;
     if (D.final_gr) {
       r++;
-      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st)) return false;
+      if (!global_relabel<KTD>(D, sh, sinks, sources, r, gen, st, Sel{false, 0})) return false;
     } else if (!fresh) {
       if (!settle(D, sh, r & 1)) return false;
     }
@@ -1532,6 +1630,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   }
   if (D.gap_every > 0)
     for (int k = tid; k <= D.n_cap; k += nthr) D.hist[k] = 0;
+  if (D.live)
+    for (int k = tid; k < D.ninst; k += nthr) D.live[k] = 0;
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
   if (ok) {
@@ -1551,9 +1651,9 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
     }
     ok = grid_sync(D, sh, 1);
   }
-  int r = 0, gen = 0;
+  int r = 0, gen = 0, epoch = 0;
   long long rnd = 0;
-  if (ok) ok = run_phase<KTD>(D, sh, D.snk, D.src, r, gen, rnd, true, st);
+  if (ok) ok = run_phase<KTD>(D, sh, D.snk, D.src, r, gen, rnd, true, st, epoch);
   if (ok && D.mode == MODE_SOLVE) {
     if (tid == 0) D.ctl->t_preflow = gtimer();
     for (int k = tid; k < D.ninst; k += nthr) {
@@ -1566,7 +1666,7 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
       ok = bfs<KTD>(D, sh, D.src, nullptr, D.ninst, false, true, gen, st, 6);
     } else {
       // Phase 2: return the excess that cannot reach t to s (s plays the sink).
-      ok = run_phase<KTD>(D, sh, D.src, D.snk, r, gen, rnd, false, st);
+      ok = run_phase<KTD>(D, sh, D.src, D.snk, r, gen, rnd, false, st, epoch);
       if (ok) {
         long long left = 0;
         for (int v = tid; v < D.n; v += nthr) {
@@ -1607,6 +1707,8 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   long long x;
   x = block_sum(st.scans_dis, sh);
   if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->scans_dis, x);
+  x = block_sum(st.scans_res, sh);
+  if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->scans_res, x);
   x = block_sum(st.scans_bfs, sh);
   if (threadIdx.x == 0 && x) atomic_add64(&D.ctl->scans_bfs, x);
   x = block_sum(st.pushes, sh);

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("cut_only", ctypes.c_int32), ("device", ctypes.c_int32), ("gr_time_ratio", ctypes.c_double),
                 ("kernel_variant", ctypes.c_int32), ("simple_rounds", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("local_lists", ctypes.c_int32), ("bfs_hops", ctypes.c_int32), ("gap_every", ctypes.c_int32),
-                ("bfs_pull", ctypes.c_int32), ("union_max_requests", ctypes.c_int32)]
+                ("bfs_pull", ctypes.c_int32), ("union_max_requests", ctypes.c_int32),
+                ("live_relabel", ctypes.c_int32)]
 
 
 class TuneSpec(ctypes.Structure):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("rounds_by_size", ctypes.c_int64 * 4), ("round_work_ms", ctypes.c_double),
                 ("round_tail_ms", ctypes.c_double), ("round_wait_ms", ctypes.c_double),
                 ("level_work_ms", ctypes.c_double), ("level_wait_ms", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("gap_lifted", ctypes.c_int64)]
+                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("gap_lifted", ctypes.c_int64),
+                ("scans_discharge_residual", ctypes.c_int64), ("global_relabels_partial", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

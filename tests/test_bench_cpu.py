@@ -11,13 +11,13 @@ sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
 
-STATS = dict(scans_discharge=1000, pushes=100, visits_discharge=50, scans_bfs=400, visits_bfs=30,
+STATS = dict(scans_discharge=1000, scans_discharge_residual=700, pushes=100, visits_discharge=50, scans_bfs=400, visits_bfs=30,
              global_relabels=2, discharge_ms=2.0, relabel_ms=1.0)
 
 
 def test_model_bytes_is_the_sum_of_its_units():
     n, m = 10, 40
-    want = (12 * 1000 + 28 * 100 + 48 * 50 + 12 * 400 + 16 * 30 + 20 * m + 28 * n + 12 * n * 2)
+    want = (4 * 1000 + 8 * 700 + 28 * 100 + 48 * 50 + 12 * 400 + 16 * 30 + 20 * m + 28 * n + 12 * n * 2)
     assert bench.model_bytes(STATS, n, m) == want
 
 
@@ -25,7 +25,7 @@ def test_phase_rooflines_split_the_kernel_bytes():
     n = 10
     ph = bench.phase_rooflines(STATS, n, peak=100.0)
     dis, bfs = ph["discharge_rounds"], ph["global_relabel_bfs"]
-    assert dis["model_bytes"] == 12 * 1000 + 28 * 100 + 48 * 50
+    assert dis["model_bytes"] == 4 * 1000 + 8 * 700 + 28 * 100 + 48 * 50
     assert bfs["model_bytes"] == 12 * 400 + 16 * 30 + 12 * n * 2
     # GB/s = bytes / (ms * 1e6); frac = that / peak
     assert dis["achieved_GBps"] == pytest.approx(dis["model_bytes"] / 2.0e6)

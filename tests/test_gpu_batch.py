@@ -87,3 +87,18 @@ def test_batch_of_grids_local_lists_and_hops(gpu, hops):
     insts = [I.grid2d(20 + 7 * k, 30 + 3 * k, 800 + k) for k in range(5)]
     insts += [I.grid3d(10 + k, 9, 6 + k, 810 + k) for k in range(3)] + [I.multiframe(3, 820, side=24)]
     check_batch(gpu, insts, gpu.default_options(bfs_hops=hops))
+
+
+@pytest.mark.parametrize("live_relabel", [0, 1])
+def test_batch_partial_relabels_agree(gpu, live_relabel):
+    """Instances of very different sizes finish at different times; with live_relabel a global relabel taken
+    while vertices are active covers only their instances. Frequent relabels (gr_freq 8) make many of them
+    partial; every instance must still get the oracle's value and S_min, and a valid flow."""
+    insts = [I.grid2d(120, 90, 900), I.layered(60, 300, 901), I.multiframe(4, 902, side=40)]
+    insts += [I.grid2d(4 + k, 5, 910 + k) for k in range(10)] + [I.layered(3, 8, 930 + k) for k in range(10)]
+    _, st = check_batch(gpu, insts, gpu.default_options(live_relabel=live_relabel, gr_freq=8.0))
+    if live_relabel:
+        assert st["global_relabels_partial"] > 0
+    else:
+        assert st["global_relabels_partial"] == 0
+    assert st["global_relabels_partial"] < st["global_relabels"]  # the first of each phase covers all

@@ -5,7 +5,9 @@ allocator, services that committed all device memory up front) keep the graph an
 memory and let the library work in its fixed static scratch area. This test calls the entry point through
 the C-ABI twice in a row and checks each result against the regular entry point (mf_solve_device): the
 flow value and the minimal source-side cut are unique, so they must match exactly; the per-slot flow must
-satisfy the flow definitions. The file is named so that pytest collects it last.
+satisfy the flow definitions. It also checks that the second call leaves the device's free memory as it
+was (nothing allocated), and that each kind of bad graph is turned away with its error code before any
+solve starts. The file is named so that pytest collects it last.
 """
 import ctypes
 
@@ -53,6 +55,7 @@ def test_no_alloc_matches_regular_entry_point_twice():
         flow = torch.zeros(csr.m, dtype=torch.int32, device=dev)
         cutw = torch.zeros((g.n + 31) // 32, dtype=torch.int32, device=dev)
         stream = torch.cuda.current_stream()
+        free = []
         for _ in range(2):
             val.fill_(-1)
             flow.fill_(-1)
@@ -62,11 +65,54 @@ def test_no_alloc_matches_regular_entry_point_twice():
                     val.data_ptr(), flow.data_ptr(), cutw.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
             assert rc == 0, mf.lib().mf_last_error()
             torch.cuda.synchronize()
+            free.append(torch.cuda.mem_get_info()[0])
             assert int(val.item()) == ref.value
             cut = mf.cut_bits_to_bool(cutw.cpu().numpy().view(np.uint32), g.n)
             assert np.array_equal(cut, ref_cut)
             f_in = np.where(csr.arc_slot >= 0, flow.cpu().numpy()[np.maximum(csr.arc_slot, 0)], 0).astype(np.int64)
             assert not oracle.check_flow(g.n, g.s, g.t, g.tail, g.head, g.cap, f_in, ref.value, cut)
+        # the first call may load the library's device code (and with it the scratch area); the second
+        # call must leave the device's free memory where the first left it
+        assert free[1] == free[0], f"free device memory changed by {free[0] - free[1]} bytes across a call"
+
+
+# Bad graphs in the int32 paired-slot layout (n = 3, s = 0, t = 2) and the code each must give. Every array
+# has the length its size argument states, so the input checks themselves stay in bounds.
+BAD_GRAPHS = {
+    "row offsets not monotone": ([0, 2, 1, 2], [1, 0], [3, 0], [1, 0], -1),
+    "head out of range": ([0, 1, 2, 2], [1, 5], [3, 0], [1, 0], -1),
+    "rev of a slot is the slot itself": ([0, 1, 2, 2], [1, 0], [3, 0], [0, 0], -1),
+    "negative capacity": ([0, 1, 2, 2], [1, 0], [-1, 0], [1, 0], -1),
+    "rev[rev[a]] != a": ([0, 2, 3, 4], [1, 2, 0, 0], [3, 4, 0, 0], [2, 2, 0, 1], -2),
+    "head[rev[a]] != tail(a)": ([0, 1, 2, 2], [1, 2], [3, 0], [1, 0], -2),
+    "pair capacities beyond INT32_MAX": ([0, 1, 2, 2], [1, 0], [2 ** 31 - 1, 1], [1, 0], -4),
+}
+
+
+@pytest.mark.parametrize("case", list(BAD_GRAPHS))
+def test_no_alloc_rejects_bad_graphs_before_solving(case):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1507_01926_gb300 import mf
+
+    fn = noalloc_fn(mf)
+    dev = torch.device("cuda:0")
+    row, head, cap, rev, code = BAD_GRAPHS[case]
+    m = len(head)
+    t32 = lambda a: torch.tensor(a, dtype=torch.int32, device=dev)  # noqa: E731
+    row_d, head_d, cap_d, rev_d = t32(row), t32(head), t32(cap), t32(rev)
+    val = torch.full((1,), -7, dtype=torch.int64, device=dev)
+    flow = torch.full((m,), -7, dtype=torch.int32, device=dev)
+    cutw = torch.full((1,), -7, dtype=torch.int32, device=dev)
+    rc = fn(3, m, row_d.data_ptr(), head_d.data_ptr(), cap_d.data_ptr(), rev_d.data_ptr(), 0, 2, val.data_ptr(),
+            flow.data_ptr(), cutw.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == code, (case, rc, mf.lib().mf_last_error())
+    # turned away before the solve: no output was written
+    assert int(val.item()) == -7 and (flow == -7).all() and int(cutw.item()) == -7
 
 
 def test_no_alloc_rejects_graphs_beyond_the_scratch_area():
