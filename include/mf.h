@@ -100,9 +100,12 @@ typedef struct mf_options {
   /* 1: run the simple synchronous rounds of Section 3 instead of the improved
    * discharge of Section 3.1: each round pushes along admissible arcs with the
    * round-start labels, then relabels every vertex still holding excess once.
-   * No arc is contested and nothing is read while it changes, so with
-   * gr_time_ratio = 0 (forced in this mode) every solve of a graph gives the
-   * same per-arc flow. More rounds than the default. */
+   * No arc is contested and nothing is read while it changes, so every solve of
+   * a graph gives the same per-arc flow: a single graph runs without the
+   * time-based relabel trigger (gr_time_ratio is taken as 0), and in a batch or
+   * service union with instance_relabel every instance keeps a relabel schedule
+   * of its own (work and round counts only), so its per-arc flow is the same
+   * alone and packed with any other instances. More rounds than the default. */
   int32_t simple_rounds;
   /* 1: capture a solve's launch sequence (control-block reset, the persistent
    * kernel, the status read-back) into a CUDA graph on the first solve and
@@ -145,12 +148,19 @@ typedef struct mf_options {
   /* Serving: most requests a lane packs into one persistent launch (0 = as
    * many as are queued and fit the budget, the default). */
   int32_t union_max_requests;
-  /* Batches and service unions: 1 (default) = a global relabel taken while
-   * some vertex is active covers only the instances that hold active vertices
-   * (the others have no excess to move, and no arc joins two instances); the
-   * first relabel of a phase and the one that confirms its end cover every
-   * instance. 0 = every global relabel covers every instance. Same results. */
-  int32_t live_relabel;
+  /* Batches and service unions: 1 (default) = every instance keeps its own
+   * global-relabel schedule, as if it were solved alone: it asks for a
+   * relabel when its relabel work since its last one exceeds
+   * (gr_alpha * n_k + m_k) / gr_freq for its own n_k and m_k, or (with
+   * gr_time_ratio > 0) when it has run more than gr_time_ratio times the
+   * depth (largest label) of its last relabel in rounds since; a relabel then
+   * covers the instances that asked, and the others keep their working sets.
+   * The first relabel of a phase and the one that confirms its end cover every
+   * instance. 0 = one schedule for the whole union (the single-graph rules on
+   * its totals), every relabel covering every instance. Same values and cuts;
+   * with simple_rounds, 1 makes every instance's per-arc flow independent of
+   * the other instances it is packed with. */
+  int32_t instance_relabel;
 } mf_options;
 
 /* Counters of the last solve. Arc scans count every slot examined by a
@@ -347,7 +357,7 @@ int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, d
  * lanes as such CTAs fit an SM, at most 8 and at most opt->blocks_per_sm when
  * that is set). mf_submit copies the instance (host arrays, paired-slot CSR)
  * and returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
- * exceed device_budget_bytes (its estimated device footprint is 65 bytes per
+ * exceed device_budget_bytes (its estimated device footprint is 77 bytes per
  * vertex + 32 bytes per slot). Lanes admit queued requests in arrival order
  * while the resident footprint stays within the budget, solve each admitted
  * group in one persistent launch, and keep the results. A request that

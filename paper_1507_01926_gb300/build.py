@@ -18,9 +18,9 @@ OUT = os.path.join(PKG, "libmf.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["mf_solver.cu", "mf_api.cu", "mf_batch.cu", "mf_service.cu", "mf_noalloc.cu", "mf_tune.cu"]
+CU_SOURCES = ["mf_solver.cu", "mf_solver_multi.cu", "mf_api.cu", "mf_batch.cu", "mf_service.cu", "mf_noalloc.cu", "mf_tune.cu"]
 CPP_SOURCES = ["mf_csr.cpp"]
-HEADERS = ["mf_device.cuh", "mf_internal.h"]
+HEADERS = ["mf_solver.cuh", "mf_device.cuh", "mf_internal.h"]
 
 
 def nvcc() -> str:

@@ -151,8 +151,8 @@ void gfree(mf_graph *g, void *p) {
 
 static void free_graph_buffers(mf_graph *g) {
   void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab, g->list[0], g->list[1], g->list[2],
-                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->ncap, g->hist,
-                g->tiles, g->voff, g->live, g->cwoff, g->d_cutw};
+                g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->vinst, g->hist,
+                g->tiles, g->voff, g->live, g->cwoff, g->d_cutw, g->inst, g->inst_work, g->inst_marcs, g->carry};
   for (void *p : ps) gfree(g, p);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (!g->lane_host) {
@@ -255,7 +255,7 @@ int launch_config(mf_graph *g) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
   if (!prop.cooperativeLaunch) return fail(MF_ERR_CUDA, "device %d lacks cooperative launch", g->device);
   int bps = 0;
-  if (solver_occupancy(g->opt.block_threads, &bps, g->opt.kernel_variant) || bps < 1)
+  if (solver_occupancy(g->opt.block_threads, &bps, g->opt.kernel_variant, g->vinst != nullptr) || bps < 1)
     return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", g->opt.block_threads);
   if (g->opt.blocks_per_sm > 0 && g->opt.blocks_per_sm < bps) bps = g->opt.blocks_per_sm;
   g->grid = bps * prop.multiProcessorCount;
@@ -278,7 +278,8 @@ int check_options(const mf_options *o) {
   if (o->gap_every < 0) return fail(MF_ERR_INVALID_ARG, "gap_every must be >= 0");
   if (o->bfs_pull < 0) return fail(MF_ERR_INVALID_ARG, "bfs_pull must be >= 0");
   if (o->union_max_requests < 0) return fail(MF_ERR_INVALID_ARG, "union_max_requests must be >= 0");
-  if (o->live_relabel != 0 && o->live_relabel != 1) return fail(MF_ERR_INVALID_ARG, "live_relabel must be 0 or 1");
+  if (o->instance_relabel != 0 && o->instance_relabel != 1)
+    return fail(MF_ERR_INVALID_ARG, "instance_relabel must be 0 or 1");
   if (o->local_lists < 0 || (o->local_lists > 1 && o->local_lists < 32) || o->local_lists > 512)
     return fail(MF_ERR_INVALID_ARG, "local_lists must be 0, 1 or in [32, 512]");
   if (o->kernel_variant < 0 || o->kernel_variant >= solver_variants())
@@ -305,7 +306,7 @@ Dev make_dev(const mf_graph *g) {
   D.n = g->n;
   D.m = (int)g->m;
   D.n_cap = g->n_cap;
-  D.ncap = g->ncap;
+  D.vinst = g->vinst;
   D.row = g->row;
   D.head = g->head;
   D.rev = g->rev;
@@ -321,7 +322,13 @@ Dev make_dev(const mf_graph *g) {
   D.ntiles = g->ntiles;
   D.voff = g->voff;
   D.live = g->live;
-  D.live_relabel = g->opt.live_relabel;
+  D.inst = g->inst;
+  D.inst_work = g->inst_work;
+  D.inst_marcs = g->inst_marcs;
+  D.carry = g->carry;
+  D.inst_relabel = (g->inst && g->opt.instance_relabel) ? 1 : 0;
+  D.gr_alpha = (double)g->opt.gr_alpha;
+  D.gr_freq = g->opt.gr_freq;
   D.ctl = g->ctl;
   D.bin_thread = g->opt.bin_thread;
   D.bin_warp = g->opt.bin_warp;
@@ -335,7 +342,9 @@ Dev make_dev(const mf_graph *g) {
   D.gap_every = (g->ninst == 1 && !D.simple && g->hist) ? g->opt.gap_every : 0;
   D.bfs_pull = g->opt.bfs_pull;
   D.hist = g->hist;
-  D.gr_time_ratio = D.simple ? 0.0 : g->opt.gr_time_ratio;
+  // the time-based trigger of a single graph depends on measured times; a union's per-instance trigger
+  // counts rounds and labels, so it stays deterministic with simple_rounds
+  D.gr_time_ratio = (D.simple && !D.inst_relabel) ? 0.0 : g->opt.gr_time_ratio;
   D.timeout_ns = (unsigned long long)g->opt.timeout_ms * 1000000ULL;
   D.mode = MODE_SOLVE;
   D.cut_only = g->opt.cut_only;
@@ -482,7 +491,7 @@ void mf_default_options(mf_options *o) {
   o->local_lists = 1;
   o->bfs_hops = 8;
   o->bfs_pull = 50;
-  o->live_relabel = 1;
+  o->instance_relabel = 1;
 }
 
 const char *mf_last_error(void) { return last_error(); }

@@ -80,7 +80,9 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
   // host packing with per-instance range checks (offsets must not leak across instances), spread over the
   // host cores by instance (each instance writes its own ranges)
   std::vector<long long> row((size_t)N + 1), rev((size_t)(M > 0 ? M : 1));
-  std::vector<int> head((size_t)(M > 0 ? M : 1)), cap((size_t)(M > 0 ? M : 1)), ncap((size_t)N), src(count), snk(count);
+  std::vector<int> head((size_t)(M > 0 ? M : 1)), cap((size_t)(M > 0 ? M : 1)), src(count), snk(count);
+  std::vector<int2> vinst((size_t)N);       // {label cap, instance} per vertex
+  std::vector<int> marcs((size_t)count, 0);  // slots with positive capacity per instance
   std::vector<int> bad(count, 0);  // 1: row offsets, 2: not monotone, 3: head, 4: rev
   std::vector<long long> maxdeg_inst(count, 0);
   parallel_instances(count, b->moff, M, [&](int k) {
@@ -97,7 +99,7 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
         return;
       }
       row[(size_t)(V + v)] = S + d.row_offsets[v];
-      ncap[(size_t)(V + v)] = d.n;
+      vinst[(size_t)(V + v)] = make_int2(d.n, k);
       if (v != d.s && v != d.t) md = std::max(md, (long long)(d.row_offsets[v + 1] - d.row_offsets[v]));
     }
     for (long long a = 0; a < d.m; a++) {
@@ -112,6 +114,7 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
       head[(size_t)(S + a)] = (int)(V + d.head[a]);
       rev[(size_t)(S + a)] = S + d.rev[a];
       cap[(size_t)(S + a)] = d.cap[a];
+      if (d.cap[a] > 0) marcs[(size_t)k]++;
     }
     src[k] = (int)(V + d.s);
     snk[k] = (int)(V + d.t);
@@ -160,7 +163,12 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
     g->ev1 = lane->ev1;
   }
   if ((rc = alloc_state(g))) return rc;
-  if ((rc = galloc(g, (void **)&g->ncap, (size_t)N * 4, "cudaMalloc label caps"))) return rc;
+  if ((rc = galloc(g, (void **)&g->vinst, (size_t)N * sizeof(int2), "cudaMalloc vertex instances"))) return rc;
+  if ((rc = galloc(g, (void **)&g->inst, (size_t)count * sizeof(InstState), "cudaMalloc instance state"))) return rc;
+  if ((rc = galloc(g, (void **)&g->inst_work, (size_t)count * INST_WORK_STRIDE * 8, "cudaMalloc instance work")))
+    return rc;
+  if ((rc = galloc(g, (void **)&g->inst_marcs, (size_t)count * 4, "cudaMalloc instance arcs"))) return rc;
+  if ((rc = galloc(g, (void **)&g->carry, (size_t)N * 4, "cudaMalloc carried entries"))) return rc;
   // instance vertex offsets and tiles (runs of at most TILE_VERTICES vertices of one instance) for the
   // global relabels that cover only some instances
   std::vector<int> voff((size_t)count + 1);
@@ -188,7 +196,10 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
   if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(rev64, rev.data(), (size_t)M * 8, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(g->head, head.data(), (size_t)M * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(g->cap, cap.data(), (size_t)M * 4, cudaMemcpyHostToDevice, g->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g->ncap, ncap.data(), (size_t)N * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->vinst, vinst.data(), (size_t)N * sizeof(int2), cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->inst_marcs, marcs.data(), (size_t)count * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->src, src.data(), (size_t)count * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->snk, snk.data(), (size_t)count * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->voff, voff.data(), voff.size() * 4, cudaMemcpyHostToDevice, g->stream);

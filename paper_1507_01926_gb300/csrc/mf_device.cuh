@@ -43,11 +43,32 @@ struct Ctl {
   int gap;             // gap relabeling: smallest label without a vertex (INT_MAX: none found yet)
   long long gap_lifted;  // vertices lifted to the label cap by gap relabeling
   long long scans_res;   // discharge scans of slots with positive residual
-  long long grs_partial;  // global relabels that covered only the live instances
+  long long grs_partial;  // global relabels that covered only some instances
+  int due_any[3];         // some instance asked for a global relabel in round rnd (by rnd % 3; multi-instance)
+  int carry_n;            // working-set entries carried over a partial global relabel
 };
 // the kernel reads cnt as one int4 and gr_req as one int2
 static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, lcnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0,
               "Ctl layout");
+
+// Relabel schedule of one instance of a multi-instance graph: each instance
+// gets its own global relabels, when the relabel work since its last one
+// exceeds its own threshold (Algorithm 1's rule with its own n and m), or when
+// it has run more rounds since its last one than gr_time_ratio times that
+// relabel's depth (its largest finite label).
+struct InstState {
+  long long thr;   // (alpha n_k + m_k) / freq
+  int last;        // round index of its last global relabel
+  int depth;       // largest finite label its last global relabel found
+  int due;         // 1: asked for a global relabel
+  int pad[3];
+};
+static_assert(sizeof(InstState) == 32, "instance state layout");
+// The relabel work of instance k since its last global relabel lives apart, at
+// Dev::inst_work[k * INST_WORK_STRIDE] (one 64-byte line each): it takes an
+// atomic add from every relabeling warp, and the state above is read by every
+// visit, which must not queue behind those atomics.
+constexpr int INST_WORK_STRIDE = 8;
 
 // Per-vertex record (addedExcess: excess received while the vertex is in the
 // working set).
@@ -71,8 +92,8 @@ static_assert(sizeof(VRec) == 32, "one sector per vertex");
 struct Dev {
   int n;        // vertices (all instances)
   int m;        // slots (all instances)
-  int n_cap;    // label cap when ncap == nullptr (single instance)
-  const int *__restrict__ ncap;  // per-vertex label cap (its instance's n), or nullptr
+  int n_cap;    // label cap when vinst == nullptr (single instance)
+  const int2 *__restrict__ vinst;  // per vertex {label cap = its instance's n, its instance}, or nullptr
   const int *__restrict__ row;   // n + 1 slot offsets
   const int *__restrict__ head;  // m
   const int *__restrict__ rev;   // m
@@ -97,7 +118,12 @@ struct Dev {
   int ntiles;
   const int *voff;
   int *live;
-  int live_relabel;  // 1: a global relabel taken while vertices are active covers only their instances
+  int inst_relabel;         // 1: per-instance relabel schedule (InstState), partial relabels carry the rest over
+  InstState *inst;          // per instance
+  long long *inst_work;     // per instance, INST_WORK_STRIDE apart
+  const int *inst_marcs;    // per instance: slots with positive capacity
+  int *carry;               // n: working-set entries of the instances a partial relabel does not cover
+  double gr_alpha, gr_freq; // Algorithm 1's constants, for the per-instance thresholds
   Ctl *ctl;
   // options
   int bin_thread;

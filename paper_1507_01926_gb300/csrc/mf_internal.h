@@ -25,7 +25,11 @@ struct mf_graph {
   unsigned long long *blab = nullptr;
   int *list[3] = {nullptr, nullptr, nullptr};
   int *src = nullptr, *snk = nullptr;
-  int *ncap = nullptr;         // per-vertex label caps (multi-instance graphs)
+  int2 *vinst = nullptr;       // multi-instance graphs: per vertex {label cap, instance}
+  mf::InstState *inst = nullptr;  // multi-instance graphs: per-instance relabel schedule
+  long long *inst_work = nullptr;  // multi-instance graphs: per-instance relabel work (INST_WORK_STRIDE apart)
+  int *inst_marcs = nullptr;   // multi-instance graphs: positive-capacity slots per instance
+  int *carry = nullptr;        // multi-instance graphs: carried working-set entries (n)
   long long *cwoff = nullptr;  // multi-instance graphs: first word of every instance's cut bitmap, ninst + 1
   unsigned *d_cutw = nullptr;  // multi-instance graphs: the instances' cut bitmaps, each from a word boundary
   int4 *tiles = nullptr;       // multi-instance graphs: vertex runs of one instance (mf::Dev::tiles)
@@ -78,7 +82,7 @@ int keep_local_limit(const mf_options &o, long long max_degree, int block_thread
 int solver_variants();
 int solver_variant_max_threads(int variant);
 int solver_variant_max_bin_thread(int variant);
-int solver_occupancy(int block_threads, int *blocks_per_sm, int variant);
+int solver_occupancy(int block_threads, int *blocks_per_sm, int variant, bool multi);
 cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant);
 int set_options(mf_graph *g, const mf_options *o);
 int autotune(mf_graph *g, const mf_tune_spec *spec, mf_options *best, double *best_ms);

@@ -177,7 +177,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
 
   // launch shape from the device, as for mf_create_graph
   int bps = 0, sms = 0;
-  if (solver_occupancy(o.block_threads, &bps, o.kernel_variant) || bps < 1)
+  if (solver_occupancy(o.block_threads, &bps, o.kernel_variant, false) || bps < 1)
     return fail(MF_ERR_CUDA, "solver kernel does not fit");
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device)) != cudaSuccess)
     return cuda_fail(e, "cudaDeviceGetAttribute");
@@ -187,7 +187,7 @@ extern "C" int mf_solve_noalloc(int32_t n, int32_t m, const int32_t *d_row, cons
   D.n = n;
   D.m = m;
   D.n_cap = n;
-  D.ncap = nullptr;
+  D.vinst = nullptr;
   D.row = d_row;
   D.head = d_head;
   D.rev = d_rev;

@@ -48,7 +48,7 @@ struct Request {
 
 // Device bytes one request occupies while resident (vertex state, slot
 // arrays, staging during creation, outputs).
-size_t footprint(long long n, long long m) { return (size_t)(65 * n + 32 * m + 65536); }
+size_t footprint(long long n, long long m) { return (size_t)(77 * n + 32 * m + 65536); }
 
 }  // namespace
 
@@ -183,7 +183,7 @@ int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_serv
   cudaError_t e = cudaSetDevice(o.device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   int bps = 0;
-  if (solver_occupancy(o.block_threads, &bps, o.kernel_variant) || bps < 1)
+  if (solver_occupancy(o.block_threads, &bps, o.kernel_variant, true) || bps < 1)
     return fail(MF_ERR_CUDA, "solver kernel does not fit %d threads per CTA", o.block_threads);
   mf_service *svc = new mf_service();
   svc->budget = device_budget_bytes;

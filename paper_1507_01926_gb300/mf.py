@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32), ("simple_rounds", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("local_lists", ctypes.c_int32), ("bfs_hops", ctypes.c_int32), ("gap_every", ctypes.c_int32),
                 ("bfs_pull", ctypes.c_int32), ("union_max_requests", ctypes.c_int32),
-                ("live_relabel", ctypes.c_int32)]
+                ("instance_relabel", ctypes.c_int32)]
 
 
 class TuneSpec(ctypes.Structure):

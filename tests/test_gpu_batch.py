@@ -89,16 +89,35 @@ def test_batch_of_grids_local_lists_and_hops(gpu, hops):
     check_batch(gpu, insts, gpu.default_options(bfs_hops=hops))
 
 
-@pytest.mark.parametrize("live_relabel", [0, 1])
-def test_batch_partial_relabels_agree(gpu, live_relabel):
-    """Instances of very different sizes finish at different times; with live_relabel a global relabel taken
-    while vertices are active covers only their instances. Frequent relabels (gr_freq 8) make many of them
-    partial; every instance must still get the oracle's value and S_min, and a valid flow."""
+@pytest.mark.parametrize("instance_relabel", [0, 1])
+@pytest.mark.parametrize("ratio", [0.0, 2.0])
+def test_batch_partial_relabels_agree(gpu, instance_relabel, ratio):
+    """Instances of very different sizes need global relabels at different times; with instance_relabel each
+    keeps its own schedule and a relabel covers only the instances that asked, carrying the others' working
+    sets over. Frequent relabels (gr_freq 8, and the round-count trigger) make many of them partial; every
+    instance must still get the oracle's value and S_min, and a valid flow."""
     insts = [I.grid2d(120, 90, 900), I.layered(60, 300, 901), I.multiframe(4, 902, side=40)]
     insts += [I.grid2d(4 + k, 5, 910 + k) for k in range(10)] + [I.layered(3, 8, 930 + k) for k in range(10)]
-    _, st = check_batch(gpu, insts, gpu.default_options(live_relabel=live_relabel, gr_freq=8.0))
-    if live_relabel:
+    opts = gpu.default_options(instance_relabel=instance_relabel, gr_freq=8.0, gr_time_ratio=ratio)
+    _, st = check_batch(gpu, insts, opts)
+    if instance_relabel:
         assert st["global_relabels_partial"] > 0
     else:
         assert st["global_relabels_partial"] == 0
     assert st["global_relabels_partial"] < st["global_relabels"]  # the first of each phase covers all
+
+
+def test_simple_rounds_flow_independent_of_the_mix(gpu):
+    """Deterministic mode in a batch: with the simple synchronous rounds and per-instance relabel schedules, an
+    instance's per-arc flow is the same solved in a batch of one and packed with other instances (which need more
+    or fewer rounds and relabels than it does)."""
+    opts = gpu.default_options(simple_rounds=1, instance_relabel=1)
+    target = I.grid2d(50, 41, 950)
+    others = [I.multiframe(3, 951, side=30), I.layered(20, 60, 952), I.grid2d(90, 80, 953), I.grid2d(6, 7, 954)]
+    (alone,), _ = check_batch(gpu, [target], opts)
+    for mix in ([target] + others, others[:2] + [target] + others[2:]):
+        res, st = check_batch(gpu, mix, opts)
+        mixed = res[mix.index(target)]
+        assert mixed.value == alone.value
+        assert np.array_equal(mixed.cut_bits, alone.cut_bits)
+        assert np.array_equal(mixed.flow, alone.flow), "per-arc flow differs between alone and mixed"

@@ -78,3 +78,35 @@ def test_budget_serialises_but_completes(gpu):
         for t, c, g in zip(tks, csrs, insts):
             assert svc.wait(t, 120000) is not None
             check(gpu, g, c, svc.poll(t))
+
+
+def test_alone_equals_mixed_per_arc_flow_in_simple_rounds(gpu):
+    """Deterministic mode: with the simple synchronous rounds (Section 3) and per-instance relabel schedules
+    (instance_relabel), a request's whole result, per-arc flow included, is the same solved alone and in a mix
+    with other requests of other sizes and kinds."""
+    opts = gpu.default_options(simple_rounds=1, instance_relabel=1)
+    target = I.multiframe(3, 61, side=40)
+    others = [I.grid2d(int(s), int(s), 400 + k) for k, s in enumerate([24, 70, 45])] + [I.multiframe(2, 410, side=30)]
+    tc = gpu.build_csr(target.n, target.tail, target.head, target.cap)
+    csrs = [gpu.build_csr(g.n, g.tail, g.head, g.cap) for g in others]
+    with gpu.Service(1 << 30, opts) as svc:
+        tk = svc.submit(tc, target.s, target.t)
+        assert svc.wait(tk, 120000) is not None
+        alone = svc.poll(tk)
+        check(gpu, target, tc, alone)
+        results = []
+        for order in (0, 1):  # the target first, then last, in one admission group each time
+            group = [(tc, target)] + list(zip(csrs, others))
+            if order:
+                group = group[1:] + group[:1]
+            tks = [svc.submit(c, g.s, g.t) for c, g in group]
+            for t in tks:
+                assert svc.wait(t, 120000) is not None
+            res = [svc.poll(t) for t in tks]
+            results.append(res[0] if order == 0 else res[-1])
+            for (c, g), r in zip(group, res):
+                check(gpu, g, c, r)
+        for mixed in results:
+            assert mixed.value == alone.value
+            assert np.array_equal(mixed.cut_bits, alone.cut_bits)
+            assert np.array_equal(mixed.flow, alone.flow), "per-arc flow differs between alone and mixed"
