@@ -185,7 +185,7 @@ def kernel_source_hash() -> str:
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_1507_01926_gb300", "csrc")
-    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("mf_solver.cuh", "mf_solver.cu", "mf_device.cuh"))
+    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("mf_solver.cuh", "mf_device.cuh"))
     return hashlib.sha256(data).hexdigest()[:16]
 
 

@@ -359,9 +359,14 @@ int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, d
  * and returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
  * exceed device_budget_bytes (its estimated device footprint is 77 bytes per
  * vertex + 32 bytes per slot). Lanes admit queued requests in arrival order
- * while the resident footprint stays within the budget, solve each admitted
- * group in one persistent launch, and keep the results. A request that
- * arrives while others are solving starts on the next free lane.
+ * while the resident footprint stays within the budget and solve each admitted
+ * group in one persistent launch. With instance_relabel (the default) every
+ * request goes through its own phases inside the launch and is complete as soon
+ * as its own results are written: the kernel flags it in mapped host memory,
+ * the lane copies its outputs while the rest of the group is still solving,
+ * and mf_wait / mf_poll see it done at once. A request that arrives while
+ * others are solving starts on the next free lane; a group's device memory is
+ * released when its launch ends.
  * mf_poll returns MF_PENDING until the ticket's result is ready, then the
  * result (outputs as for mf_solve, each nullable; the solve's error code if it
  * failed) and forgets the ticket. mf_wait blocks until the ticket is done

@@ -1,6 +1,7 @@
 """Builds libmf.so (the C-ABI solver library) in-tree with nvcc for sm_103a.
 
-Translation units are compiled in parallel and linked into ``paper_1507_01926_gb300/libmf.so``.
+Translation units are compiled in parallel (only those whose source or headers changed) and linked into
+``paper_1507_01926_gb300/libmf.so``.
 Nothing is installed; the library is loaded from this directory.
 """
 from __future__ import annotations
@@ -16,9 +17,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libmf.so")
 BUILD = os.path.join(PKG, "_build")
+# the same library with every gather index of the solver checked (MF_CHECK_BOUNDS), for tests
+OUT_CHECK = os.path.join(PKG, "libmf_check.so")
+BUILD_CHECK = os.path.join(PKG, "_build_check")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["mf_solver.cu", "mf_solver_multi.cu", "mf_api.cu", "mf_batch.cu", "mf_service.cu", "mf_noalloc.cu", "mf_tune.cu"]
+CU_SOURCES = ["mf_kernels_m0.cu", "mf_kernels_m1.cu", "mf_kernels_s0.cu", "mf_kernels_s1.cu", "mf_solver.cu", "mf_api.cu", "mf_batch.cu", "mf_service.cu", "mf_noalloc.cu", "mf_tune.cu"]
 CPP_SOURCES = ["mf_csr.cpp"]
 HEADERS = ["mf_solver.cuh", "mf_device.cuh", "mf_internal.h"]
 
@@ -35,44 +39,58 @@ def _inputs():
     return srcs + [os.path.join(INCLUDE, "mf.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(OUT):
+def up_to_date(out: str = OUT) -> bool:
+    if not os.path.exists(out):
         return False
-    t = os.path.getmtime(OUT)
+    t = os.path.getmtime(out)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Builds libmf.so, or with check=True libmf_check.so (the solver compiled with MF_CHECK_BOUNDS: a gather
+    index outside its array is reported as MF_ERR_INTERNAL with the source line and the index, no trap)."""
+    out, build_dir = (OUT_CHECK, BUILD_CHECK) if check else (OUT, BUILD)
+    if not force and up_to_date(out):
+        return out
+    os.makedirs(build_dir, exist_ok=True)
     nv = nvcc()
-    common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC]
+    common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC] + (["-DMF_CHECK_BOUNDS"] if check else [])
     procs = []
     objs = []
+    # an object is rebuilt when its source, a header or this script is newer than it (or force)
+    deps = max(os.path.getmtime(p) for p in [os.path.join(CSRC, h) for h in HEADERS]
+               + [os.path.join(INCLUDE, "mf.h"), os.path.abspath(__file__)])
+
+    def stale(src, obj):
+        return force or not os.path.exists(obj) or os.path.getmtime(obj) < max(deps, os.path.getmtime(src))
+
     for f in CU_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
+        o = os.path.join(build_dir, f + ".o")
+        objs.append(o)
+        if not stale(os.path.join(CSRC, f), o):
+            continue
         cmd = [nv, *ARCH, "-lineinfo", *common, "-Xcompiler", "-fPIC", "-c", os.path.join(CSRC, f), "-o", o]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(o)
     for f in CPP_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
+        o = os.path.join(build_dir, f + ".o")
+        objs.append(o)
+        if not stale(os.path.join(CSRC, f), o):
+            continue
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, f), "-o", o]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(o)
     failed = []
     for cmd, p in procs:
-        out, _ = p.communicate()
+        log, _ = p.communicate()
         if verbose or p.returncode:
-            sys.stderr.write(out.decode(errors="replace"))
+            sys.stderr.write(log.decode(errors="replace"))
         if p.returncode:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("libmf build failed:\n" + "\n".join(failed))
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     subprocess.check_call([nv, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -152,7 +152,8 @@ void gfree(mf_graph *g, void *p) {
 static void free_graph_buffers(mf_graph *g) {
   void *ps[] = {g->row, g->head, g->rev, g->cap, g->rr, g->vs, g->blab, g->list[0], g->list[1], g->list[2],
                 g->src, g->snk, g->ctl, g->d_value, g->d_flow, g->d_cut, g->vinst, g->hist,
-                g->tiles, g->voff, g->live, g->cwoff, g->d_cutw, g->inst, g->inst_work, g->inst_marcs, g->carry};
+                g->tiles, g->voff, g->live, g->cwoff, g->d_cutw, g->inst, g->inst_work, g->inst_marcs, g->carry,
+                g->gseed, g->gblocker};
   for (void *p : ps) gfree(g, p);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (!g->lane_host) {
@@ -326,6 +327,9 @@ Dev make_dev(const mf_graph *g) {
   D.inst_work = g->inst_work;
   D.inst_marcs = g->inst_marcs;
   D.carry = g->carry;
+  D.gseed = g->gseed;
+  D.gblock = g->gblocker;
+  D.cwoff = g->cwoff;
   D.inst_relabel = (g->inst && g->opt.instance_relabel) ? 1 : 0;
   D.gr_alpha = (double)g->opt.gr_alpha;
   D.gr_freq = g->opt.gr_freq;
@@ -398,6 +402,15 @@ static int ensure_graph(mf_graph *g, const Dev &D, cudaStream_t st) {
 
 // Runs the persistent kernel once with D; fills g->h_ctl and g->stats.
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
+  const int rc = launch_kernel(g, D, st);
+  if (rc) return rc;
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solver");
+  return finish_kernel(g);
+}
+
+// Enqueues one solve with D on st (see run_kernel); returns without waiting.
+int launch_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   cudaError_t e;
   if (g->opt.gap_every > 0 && g->ninst == 1 && !g->opt.simple_rounds && !g->hist) {
     // label counts for gap relabeling, zeroed by the kernel before use
@@ -416,8 +429,11 @@ int run_kernel(mf_graph *g, Dev &D, cudaStream_t st) {
   } else {
     e = enqueue_solve(g, D, st, true);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "solver");
+  return e == cudaSuccess ? MF_OK : cuda_fail(e, "solver launch");
+}
+
+// After a launch finished: statistics and status from the control block.
+int finish_kernel(mf_graph *g) {
   const Ctl &c = *g->h_ctl;
   float ms = 0;
   cudaEventElapsedTime(&ms, g->ev0, g->ev1);
@@ -458,6 +474,9 @@ int device_status(const Ctl &c) {
                                 "discharge barrier", "apply barrier", "cut BFS (preflow)", "excess check",
                                 "phase-2 excess check", "cut BFS", "round limit", "list capacity",
                                 "settle barrier", "gap relabeling"};
+  if (c.err == MF_ERR_INTERNAL && c.err_where >= 1000)  // a build with gather checks (MF_CHECK_BOUNDS)
+    return fail(MF_ERR_INTERNAL, "gather index %lld out of bounds at mf_solver.cuh line %d", c.bad_index,
+                c.err_where - 1000);
   const char *w = (c.err_where >= 0 && c.err_where <= 13) ? where[c.err_where] : "?";
   if (c.err == MF_ERR_TIMEOUT) return fail(MF_ERR_TIMEOUT, "device wait timed out (%s)", w);
   if (c.err == MF_ERR_ITER_LIMIT) return fail(MF_ERR_ITER_LIMIT, "round limit reached (%lld rounds)", c.rounds);

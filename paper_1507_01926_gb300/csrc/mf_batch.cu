@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -169,6 +170,8 @@ int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *op
     return rc;
   if ((rc = galloc(g, (void **)&g->inst_marcs, (size_t)count * 4, "cudaMalloc instance arcs"))) return rc;
   if ((rc = galloc(g, (void **)&g->carry, (size_t)N * 4, "cudaMalloc carried entries"))) return rc;
+  if ((rc = galloc(g, (void **)&g->gseed, (size_t)count * 4, "cudaMalloc relabel seeds"))) return rc;
+  if ((rc = galloc(g, (void **)&g->gblocker, (size_t)count * 4, "cudaMalloc relabel blockers"))) return rc;
   // instance vertex offsets and tiles (runs of at most TILE_VERTICES vertices of one instance) for the
   // global relabels that cover only some instances
   std::vector<int> voff((size_t)count + 1);
@@ -248,9 +251,55 @@ __global__ void k_split_cut(const unsigned *cut, long long words, const int *vof
   }
 }
 
+// True when the kernel can run every instance's phases, cut and outputs itself
+// (per-instance relabel schedules, full solves), writing each instance's cut
+// bitmap straight into its word-aligned run of g->d_cutw. Service lanes use it
+// to hand out results early; mf_batch_solve, which returns all results at once,
+// keeps the phases shared (fewer global relabels).
+static bool per_instance_possible(const mf_graph *g) { return g->inst && g->opt.instance_relabel && !g->opt.cut_only; }
+
+// Device outputs of a union solve and the Dev that writes them (per_instance:
+// the kernel runs every instance's phases and outputs on its own).
+static int prepare_union(mf_batch *b, bool want_flow, bool want_cut, bool per_instance, Dev &D) {
+  mf_graph *g = b->g;
+  int rc;
+  if (want_flow && !g->d_flow && (rc = galloc(g, (void **)&g->d_flow, (size_t)g->m * 4, "cudaMalloc flow output")))
+    return rc;
+  const size_t words = ((size_t)g->n + 31) / 32;
+  if (want_cut && !per_instance && !g->d_cut &&
+      (rc = galloc(g, (void **)&g->d_cut, words * 4, "cudaMalloc cut output")))
+    return rc;
+  if (want_cut && !g->d_cutw &&
+      (rc = galloc(g, (void **)&g->d_cutw, (size_t)b->cwoff[(size_t)b->count] * 4, "cudaMalloc cut outputs")))
+    return rc;
+  D = make_dev(g);
+  D.out_value = g->d_value;
+  D.out_flow = want_flow ? g->d_flow : nullptr;
+  D.union_phases = per_instance ? 1 : 0;
+  if (per_instance)
+    D.out_cutw = want_cut ? g->d_cutw : nullptr;
+  else
+    D.out_cut = want_cut ? g->d_cut : nullptr;
+  return MF_OK;
+}
+
+// Copies instance k's outputs (value, its slice of the per-slot flow, its cut
+// bitmap) to host memory on stream st (enqueued only).
+static cudaError_t copy_instance(mf_batch *b, int k, cudaStream_t st, int64_t *value, int32_t *flow, uint32_t *cut) {
+  mf_graph *g = b->g;
+  cudaError_t e = cudaSuccess;
+  if (value) e = cudaMemcpyAsync(value, g->d_value + k, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && flow && b->m[(size_t)k] > 0)
+    e = cudaMemcpyAsync(flow, g->d_flow + b->moff[(size_t)k], (size_t)b->m[(size_t)k] * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && cut)
+    e = cudaMemcpyAsync(cut, g->d_cutw + b->cwoff[(size_t)k],
+                        (size_t)(b->cwoff[(size_t)k + 1] - b->cwoff[(size_t)k]) * 4, cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
 // Solves the packed union and copies the outputs of every instance to its host
 // arrays: values, the instance's slice of the per-slot flow, and its cut
-// bitmap (split on the device).
+// bitmap (split on the device, or written per instance by the kernel).
 int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits) {
   mf_graph *g = b->g;
   bool want_flow = false, want_cut = false;
@@ -261,21 +310,13 @@ int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cu
   if (g->opt.cut_only && want_flow) return fail(MF_ERR_INVALID_ARG, "cut_only solves produce no per-arc flow");
   cudaError_t e = cudaSetDevice(g->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  int rc;
-  if (want_flow && !g->d_flow && (rc = galloc(g, (void **)&g->d_flow, (size_t)g->m * 4, "cudaMalloc flow output")))
-    return rc;
-  const size_t words = ((size_t)g->n + 31) / 32;
-  if (want_cut && !g->d_cut && (rc = galloc(g, (void **)&g->d_cut, words * 4, "cudaMalloc cut output"))) return rc;
-  if (want_cut && !g->d_cutw &&
-      (rc = galloc(g, (void **)&g->d_cutw, (size_t)b->cwoff[(size_t)b->count] * 4, "cudaMalloc cut outputs")))
-    return rc;
-  Dev D = make_dev(g);
-  D.out_value = g->d_value;
-  D.out_flow = want_flow ? g->d_flow : nullptr;
-  D.out_cut = want_cut ? g->d_cut : nullptr;
+  Dev D;
+  int rc = prepare_union(b, want_flow, want_cut, false, D);
+  if (rc) return rc;
   rc = run_kernel(g, D, g->stream);
   if (rc) return rc;
   if (want_cut) {
+    const size_t words = ((size_t)g->n + 31) / 32;
     const long long total = b->cwoff[(size_t)b->count];
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
     k_split_cut<<<blocks > 0 ? blocks : 1, 256, 0, g->stream>>>(g->d_cut, (long long)words, g->voff, g->cwoff,
@@ -284,21 +325,79 @@ int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cu
     if (e != cudaSuccess) return cuda_fail(e, "cut split");
   }
   std::vector<long long> vals((size_t)b->count);
-  e = cudaMemcpyAsync(vals.data(), g->d_value, (size_t)b->count * 8, cudaMemcpyDeviceToHost, g->stream);
-  for (int k = 0; k < b->count && e == cudaSuccess; k++) {
-    if (want_flow && arc_flows[k] && b->m[(size_t)k] > 0)
-      e = cudaMemcpyAsync(arc_flows[k], g->d_flow + b->moff[(size_t)k], (size_t)b->m[(size_t)k] * 4,
-                          cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess && want_cut && cut_bits[k])
-      e = cudaMemcpyAsync(cut_bits[k], g->d_cutw + b->cwoff[(size_t)k],
-                          (size_t)(b->cwoff[(size_t)k + 1] - b->cwoff[(size_t)k]) * 4, cudaMemcpyDeviceToHost,
-                          g->stream);
-  }
+  for (int k = 0; k < b->count && e == cudaSuccess; k++)
+    e = copy_instance(b, k, g->stream, nullptr, want_flow ? arc_flows[k] : nullptr, want_cut ? cut_bits[k] : nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(vals.data(), g->d_value, (size_t)b->count * 8, cudaMemcpyDeviceToHost, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of the outputs");
   if (values)
     for (int k = 0; k < b->count; k++) values[k] = vals[(size_t)k];
   return MF_OK;
+}
+
+// Service lanes: solves the union like solve_union, but hands every instance
+// its results as soon as the kernel has written them (its done flag in the
+// lane's mapped host memory), while the other instances are still being
+// solved: their outputs are copied on the lane's copy stream, then
+// on_done(k, MF_OK) runs. When the kernel has finished, instances without a
+// result get the launch's error (on_done(k, rc)). Returns the launch's status.
+int solve_union_streaming(mf_batch *b, const LaneHost &lane, int64_t *values, int32_t **arc_flows,
+                          uint32_t **cut_bits, void (*on_done)(void *ctx, int k, int rc), void *ctx) {
+  mf_graph *g = b->g;
+  if (!per_instance_possible(g) || b->count > lane.done_cap) {
+    const int rc = solve_union(b, values, arc_flows, cut_bits);
+    for (int k = 0; k < b->count; k++) on_done(ctx, k, rc);
+    return rc;
+  }
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  Dev D;
+  int rc = prepare_union(b, true, true, true, D);
+  if (rc) return rc;
+  memset(lane.h_done, 0, (size_t)b->count * sizeof(unsigned));
+  D.done_flag = lane.d_done;
+  rc = launch_kernel(g, D, g->stream);
+  if (rc) return rc;
+  std::vector<char> given((size_t)b->count, 0);
+  int left = b->count;
+  auto deliver_ready = [&]() -> cudaError_t {
+    std::vector<int> ready;
+    for (int k = 0; k < b->count; k++)
+      if (!given[(size_t)k] && ((volatile unsigned *)lane.h_done)[k]) ready.push_back(k);
+    if (ready.empty()) return cudaSuccess;
+    cudaError_t ce = cudaSuccess;
+    for (int k : ready)
+      if (ce == cudaSuccess) ce = copy_instance(b, k, lane.copy, values + k, arc_flows[k], cut_bits[k]);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(lane.copy);
+    if (ce != cudaSuccess) return ce;
+    for (int k : ready) {
+      given[(size_t)k] = 1;
+      left--;
+      on_done(ctx, k, MF_OK);
+    }
+    return cudaSuccess;
+  };
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(g->stream);
+    if ((e = deliver_ready()) != cudaSuccess) break;
+    if (q != cudaErrorNotReady) {
+      e = q;
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  rc = e == cudaSuccess ? finish_kernel(g) : cuda_fail(e, "solver");
+  if (rc == MF_OK && left > 0) {  // the kernel finished without flagging some instance: copy them all now
+    for (int k = 0; k < b->count && e == cudaSuccess; k++)
+      if (!given[(size_t)k]) e = copy_instance(b, k, lane.copy, values + k, arc_flows[k], cut_bits[k]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lane.copy);
+    if (e != cudaSuccess) rc = cuda_fail(e, "device-to-host copy of the outputs");
+  }
+  for (int k = 0; k < b->count; k++)
+    if (!given[(size_t)k]) on_done(ctx, k, rc);
+  return rc;
 }
 
 mf_batch *new_batch() { return new mf_batch(); }

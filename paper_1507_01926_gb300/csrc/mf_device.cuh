@@ -46,6 +46,10 @@ struct Ctl {
   long long grs_partial;  // global relabels that covered only some instances
   int due_any[3];         // some instance asked for a global relabel in round rnd (by rnd % 3; multi-instance)
   int carry_n;            // working-set entries carried over a partial global relabel
+  int ph2_started;        // unions: a relabel ended the preflow of some instances (they need a relabel from s)
+  int cut_pending;        // unions: a relabel ended the flow phase of some instances (they need their cut)
+  int done_cnt;           // unions: instances whose results are written
+  long long bad_index;    // builds with MF_CHECK_BOUNDS: the first gather index found outside its array
 };
 // the kernel reads cnt as one int4 and gr_req as one int2
 static_assert(offsetof(Ctl, cnt) % 16 == 0 && offsetof(Ctl, lcnt) % 16 == 0 && offsetof(Ctl, gr_req) % 8 == 0,
@@ -61,7 +65,9 @@ struct InstState {
   int last;        // round index of its last global relabel
   int depth;       // largest finite label its last global relabel found
   int due;         // 1: asked for a global relabel
-  int pad[3];
+  int ph;          // its phase: 1 preflow (toward t), 2 flow (excess back to s), 3 cut pending, 4 done
+  int act;         // working-set entries its last global relabel found
+  int pad;
 };
 static_assert(sizeof(InstState) == 32, "instance state layout");
 // The relabel work of instance k since its last global relabel lives apart, at
@@ -123,6 +129,13 @@ struct Dev {
   long long *inst_work;     // per instance, INST_WORK_STRIDE apart
   const int *inst_marcs;    // per instance: slots with positive capacity
   int *carry;               // n: working-set entries of the instances a partial relabel does not cover
+  int *gseed, *gblock;      // per instance: the seed and the blocker of its next global relabel (t and s in the
+                            // preflow, s and t in the flow phase)
+  unsigned *out_cutw;       // per-instance cut bitmaps, instance k's from word cwoff[k] (nullable)
+  const long long *cwoff;
+  volatile unsigned *done_flag;  // per instance, in mapped host memory (nullable): 1 once its results are written
+  int union_phases;         // 1: every instance goes through its own phases, cut and outputs (service lanes, which
+                            // hand each request its results as soon as they are written)
   double gr_alpha, gr_freq; // Algorithm 1's constants, for the per-instance thresholds
   Ctl *ctl;
   // options

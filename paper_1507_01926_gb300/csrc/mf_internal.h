@@ -30,6 +30,7 @@ struct mf_graph {
   long long *inst_work = nullptr;  // multi-instance graphs: per-instance relabel work (INST_WORK_STRIDE apart)
   int *inst_marcs = nullptr;   // multi-instance graphs: positive-capacity slots per instance
   int *carry = nullptr;        // multi-instance graphs: carried working-set entries (n)
+  int *gseed = nullptr, *gblocker = nullptr;  // multi-instance graphs: per-instance relabel seed and blocker
   long long *cwoff = nullptr;  // multi-instance graphs: first word of every instance's cut bitmap, ninst + 1
   unsigned *d_cutw = nullptr;  // multi-instance graphs: the instances' cut bitmaps, each from a word boundary
   int4 *tiles = nullptr;       // multi-instance graphs: vertex runs of one instance (mf::Dev::tiles)
@@ -63,6 +64,10 @@ struct LaneHost {
   cudaMemPool_t pool;
   Ctl *h_ctl;
   cudaEvent_t ev0, ev1;
+  cudaStream_t copy;       // copies of finished requests' results while the kernel runs
+  unsigned *h_done;        // mapped host memory: per-instance done flags the kernel sets
+  unsigned *d_done;        // their device address
+  int done_cap;            // flags available
 };
 
 int fail(int code, const char *fmt, ...);
@@ -78,6 +83,8 @@ Dev make_dev(const mf_graph *g);
 long long relabel_threshold(const mf_options &o, long long n, long long m_arcs);
 int device_status(const Ctl &c);
 int run_kernel(mf_graph *g, Dev &D, cudaStream_t st);
+int launch_kernel(mf_graph *g, Dev &D, cudaStream_t st);
+int finish_kernel(mf_graph *g);
 int keep_local_limit(const mf_options &o, long long max_degree, int block_threads);
 int solver_variants();
 int solver_variant_max_threads(int variant);

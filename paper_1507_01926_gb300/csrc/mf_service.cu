@@ -72,23 +72,68 @@ namespace mf {
 int create_union(int32_t count, const mf_graph_desc *descs, const mf_options *opt, cudaStream_t stream,
                  mf_batch *b, const LaneHost *lane);
 int solve_union(mf_batch *b, int64_t *values, int32_t **arc_flows, uint32_t **cut_bits);
+int solve_union_streaming(mf_batch *b, const LaneHost &lane, int64_t *values, int32_t **arc_flows,
+                          uint32_t **cut_bits, void (*on_done)(void *ctx, int k, int rc), void *ctx);
 mf_batch *new_batch();
 void destroy_union(mf_batch *b);
 const char *last_error();
 }  // namespace mf
+
+namespace {
+// A lane's view of the requests of the union it is solving.
+struct LaneUnion {
+  mf_service *svc;
+  std::vector<Request *> *batch;
+  std::vector<int64_t> *values;
+};
+
+// Completes request k of the lane's union (its outputs are in place): called as
+// soon as the kernel has written them, while the rest of the union may still
+// be solving.
+void lane_on_done(void *ctx, int k, int rc) {
+  LaneUnion *u = static_cast<LaneUnion *>(ctx);
+  Request *r = (*u->batch)[(size_t)k];
+  const std::string err = rc ? std::string(last_error()) : std::string();
+  {
+    std::lock_guard<std::mutex> lk(u->svc->mu);
+    r->value = (*u->values)[(size_t)k];
+    r->rc = rc;
+    r->err = err;
+    r->done = true;
+    r->t_done = Clock::now();
+    // the instance itself is no longer needed
+    std::vector<int64_t>().swap(r->row);
+    std::vector<int64_t>().swap(r->rev);
+    std::vector<int32_t>().swap(r->head);
+    std::vector<int32_t>().swap(r->cap);
+  }
+  u->svc->cv_done.notify_all();
+}
+}  // namespace
 
 static void lane_main(mf_service *svc, int lane) {
   mf_options o = svc->opt;
   cudaSetDevice(o.device);
   cudaStream_t stream = nullptr;
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
-  LaneHost lh{svc->pool, nullptr, nullptr, nullptr};
+  LaneHost lh{svc->pool, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   cudaMallocHost((void **)&lh.h_ctl, sizeof(Ctl));
   cudaEventCreate(&lh.ev0);
   cudaEventCreate(&lh.ev1);
+  cudaStreamCreateWithFlags(&lh.copy, cudaStreamNonBlocking);
+  // done flags the kernel sets per instance, read by this thread while the kernel runs (unions of more
+  // instances than this are solved without early delivery)
+  const int kDoneCap = 1 << 16;
+  if (cudaHostAlloc((void **)&lh.h_done, kDoneCap * sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
+      cudaHostGetDevicePointer((void **)&lh.d_done, lh.h_done, 0) == cudaSuccess)
+    lh.done_cap = kDoneCap;
+  else
+    cudaGetLastError();
   for (;;) {
     std::vector<Request *> batch;
     size_t bytes = 0;
+    long long adm_n = 0, adm_m = 0;  // the admitted requests' sizes (a request may be handed out and freed by
+                                     // mf_poll while the rest of its union is still being solved)
     {
       std::unique_lock<std::mutex> lk(svc->mu);
       svc->cv_work.wait(lk, [&] {
@@ -111,6 +156,8 @@ static void lane_main(mf_service *svc, int lane) {
       svc->in_use += bytes;
       svc->resident_n += nn;
       svc->resident_m += mm;
+      adm_n = nn;
+      adm_m = mm;
       if (!svc->pending.empty()) svc->cv_work.notify_one();  // another lane may take the rest
     }
     std::vector<mf_graph_desc> descs(batch.size());
@@ -128,41 +175,29 @@ static void lane_main(mf_service *svc, int lane) {
       cu[i] = batch[i]->cut.data();
     }
     mf_batch *b = new_batch();
-    int rc = (lh.h_ctl && lh.ev0 && lh.ev1) ? create_union((int32_t)batch.size(), descs.data(), &o, stream, b, &lh)
-                                            : fail(MF_ERR_CUDA, "service lane set-up failed");
-    if (rc == MF_OK) rc = solve_union(b, values.data(), fl.data(), cu.data());
-    std::string err = rc ? std::string(last_error()) : std::string();
+    LaneUnion u{svc, &batch, &values};
+    int rc = (lh.h_ctl && lh.ev0 && lh.ev1 && lh.copy)
+                 ? create_union((int32_t)batch.size(), descs.data(), &o, stream, b, &lh)
+                 : fail(MF_ERR_CUDA, "service lane set-up failed");
+    if (rc == MF_OK)  // every request completes as soon as its own results are written
+      solve_union_streaming(b, lh, values.data(), fl.data(), cu.data(), lane_on_done, &u);
+    else
+      for (size_t i = 0; i < batch.size(); i++) lane_on_done(&u, (int)i, rc);
     destroy_union(b);
-    long long nn = 0, mm = 0;
-    {
+    {  // every request of the union is done (and may be gone): only the admitted totals are used here
       std::lock_guard<std::mutex> lk(svc->mu);
-      const auto now = Clock::now();
-      for (size_t i = 0; i < batch.size(); i++) {
-        Request *r = batch[i];
-        r->value = values[i];
-        r->rc = rc;
-        r->err = err;
-        r->done = true;
-        r->t_done = now;
-        nn += r->n;
-        mm += r->m;
-        // the instance itself is no longer needed
-        std::vector<int64_t>().swap(r->row);
-        std::vector<int64_t>().swap(r->rev);
-        std::vector<int32_t>().swap(r->head);
-        std::vector<int32_t>().swap(r->cap);
-      }
       svc->in_use -= bytes;
-      svc->resident_n -= nn;
-      svc->resident_m -= mm;
+      svc->resident_n -= adm_n;
+      svc->resident_m -= adm_m;
     }
-    svc->cv_done.notify_all();
     svc->cv_work.notify_all();
   }
   if (stream) cudaStreamSynchronize(stream);
   if (lh.h_ctl) cudaFreeHost(lh.h_ctl);
   if (lh.ev0) cudaEventDestroy(lh.ev0);
   if (lh.ev1) cudaEventDestroy(lh.ev1);
+  if (lh.copy) cudaStreamDestroy(lh.copy);
+  if (lh.h_done) cudaFreeHost(lh.h_done);
   if (stream) cudaStreamDestroy(stream);
 }
 

@@ -1,34 +1,36 @@
 // Synchronous parallel push-relabel solver (arXiv:1507.01926, Section 3.1 and
-// Algorithm 1, global relabels by Algorithm 2): the kernel instances for single
-// graphs and the host side of the launch (register-budget variants, occupancy,
-// cooperative launch). The kernel itself is in mf_solver.cuh; the instances for
-// batches and service unions are compiled in mf_solver_multi.cu.
+// Algorithm 1, global relabels by Algorithm 2): the host side of the launch
+// (register-budget variants, occupancy, cooperative launch). The kernel is in
+// mf_solver.cuh; its instances (single graphs and unions, five register
+// budgets each) are compiled in mf_kernels_*.cu.
 #include "mf_solver.cuh"
 
 namespace mf {
 
-template __global__ void solve_kernel<512, 1, KT, false>(Dev);
-template __global__ void solve_kernel<256, 3, KT, false>(Dev);
-template __global__ void solve_kernel<256, 4, KT, false>(Dev);
-template __global__ void solve_kernel<512, 2, KT, false>(Dev);
-template __global__ void solve_kernel<256, 1, 16, false>(Dev);
-
 // ------------------------------------------------------------------ host side
 
-const void *solver_multi_fn(int variant);  // mf_solver_multi.cu
+// kernel entry points by variant, from the units that instantiate them (nullptr if the unit has not the variant)
+const void *solver_kernel_s0(int v);
+const void *solver_kernel_s1(int v);
+const void *solver_kernel_m0(int v);
+const void *solver_kernel_m1(int v);
+
+static const void *kernel_fn(int variant, bool multi) {
+  const void *f = multi ? solver_kernel_m0(variant) : solver_kernel_s0(variant);
+  return f ? f : (multi ? solver_kernel_m1(variant) : solver_kernel_s1(variant));
+}
 
 struct Variant {
-  const void *fn;  // single graphs (the batch and union instances: solver_multi_fn)
   int max_threads;
   int max_bin_thread;  // KTD
 };
 
 static const Variant kVariants[] = {
-    {(const void *)solve_kernel<512, 1, KT, false>, 512, KT},  // up to 128 registers
-    {(const void *)solve_kernel<256, 3, KT, false>, 256, KT},  // up to 85
-    {(const void *)solve_kernel<256, 4, KT, false>, 256, KT},  // up to 64
-    {(const void *)solve_kernel<512, 2, KT, false>, 512, KT},  // up to 64
-    {(const void *)solve_kernel<256, 1, 16, false>, 256, 16},  // up to 255; one thread discharges up to 16 slots
+    {512, KT},  // 0: __launch_bounds__(512, 1), up to 128 registers
+    {256, KT},  // 1: (256, 3), up to 85
+    {256, KT},  // 2: (256, 4), up to 64
+    {512, KT},  // 3: (512, 2), up to 64
+    {256, 16},  // 4: (256, 1), up to 255; one thread discharges up to 16 slots
 };
 constexpr int NUM_VARIANTS = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -51,7 +53,7 @@ int keep_local_limit(const mf_options &o, long long max_degree, int block_thread
 
 int solver_occupancy(int block_threads, int *blocks_per_sm, int variant, bool multi) {
   if (variant < 0 || variant >= NUM_VARIANTS) return -1;
-  const void *fn = multi ? solver_multi_fn(variant) : kVariants[variant].fn;
+  const void *fn = kernel_fn(variant, multi);
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block_threads, 0);
   return e == cudaSuccess ? 0 : -1;
 }
@@ -59,7 +61,7 @@ int solver_occupancy(int block_threads, int *blocks_per_sm, int variant, bool mu
 cudaError_t launch_solver(const Dev &D, int grid, int block, cudaStream_t stream, int variant) {
   Dev d = D;
   void *args[] = {&d};
-  const void *fn = D.vinst ? solver_multi_fn(variant) : kVariants[variant].fn;
+  const void *fn = kernel_fn(variant, D.vinst != nullptr);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, stream);
 }
 

@@ -81,12 +81,38 @@ __device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigne
 
 __device__ __forceinline__ int vol_read(const int *p) { return *(const volatile int *)p; }
 
+// Index checks of the gathers (a build with MF_CHECK_BOUNDS, for tests): an
+// index outside its array is recorded in the error word (MF_ERR_INTERNAL, the
+// solver source line in err_where and the index in bad_index, first one wins)
+// and replaced by 0, so the access stays inside the array and the solve ends
+// at its next grid barrier; no trap. Without MF_CHECK_BOUNDS the macros are the
+// index itself.
+#ifdef MF_CHECK_BOUNDS
+static __device__ __noinline__ long long mf_bad_index(const Dev &D, long long i, int line) {
+  if (atomicCAS(&D.ctl->err, 0, MF_ERR_INTERNAL) == 0) {
+    atomicExch(&D.ctl->err_where, 1000 + line);
+    atomicExch(reinterpret_cast<unsigned long long *>(&D.ctl->bad_index), (unsigned long long)i);
+  }
+  return 0;
+}
+#define MF_CHECKED(D, i, lim) \
+  (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(lim)) ? (i)                     \
+                                                                              : (decltype((i) + 0))mf_bad_index(D, (i), __LINE__))
+#define MF_SLOT(D, a) MF_CHECKED(D, a, (D).m)
+#define MF_VTX(D, v) MF_CHECKED(D, v, (D).n)
+#define MF_ROW(D, v) MF_CHECKED(D, v, (D).n + 1)
+#else
+#define MF_SLOT(D, a) (a)
+#define MF_VTX(D, v) (v)
+#define MF_ROW(D, v) (v)
+#endif
+
 // label slot p / active stamp slot p of v
-__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return reinterpret_cast<int *>(D.vs + v) + 2 * p; }
+__device__ __forceinline__ int *lab_ptr(const Dev &D, int v, int p) { return reinterpret_cast<int *>(D.vs + MF_VTX(D, v)) + 2 * p; }
 __device__ __forceinline__ int *act_ptr(const Dev &D, int v, int p) { return lab_ptr(D, v, p) + 1; }
 // {label, stamp} of v in slot p
 __device__ __forceinline__ int2 load_slot(const Dev &D, int p, int v) {
-  return __ldcg(reinterpret_cast<const int2 *>(D.vs + v) + p);
+  return __ldcg(reinterpret_cast<const int2 *>(D.vs + MF_VTX(D, v)) + p);
 }
 
 __device__ __forceinline__ int cap_of(const Dev &D, int v) { return D.vinst ? __ldg(&D.vinst[v]).x : D.n_cap; }
@@ -101,10 +127,10 @@ __device__ __forceinline__ int2 vinst_of(const Dev &D, int v) {
 }
 
 // excess and addedExcess of v share one 16-byte entry
-__device__ __forceinline__ long long *exc_ptr(const Dev &D, int v) { return &D.vs[v].exc; }
-__device__ __forceinline__ long long *add_ptr(const Dev &D, int v) { return &D.vs[v].added; }
+__device__ __forceinline__ long long *exc_ptr(const Dev &D, int v) { return &D.vs[MF_VTX(D, v)].exc; }
+__device__ __forceinline__ long long *add_ptr(const Dev &D, int v) { return &D.vs[MF_VTX(D, v)].added; }
 __device__ __forceinline__ longlong2 load_ea(const Dev &D, int v) {
-  return __ldcg(reinterpret_cast<const longlong2 *>(&D.vs[v].exc));
+  return __ldcg(reinterpret_cast<const longlong2 *>(&D.vs[MF_VTX(D, v)].exc));
 }
 
 __device__ __forceinline__ void set_err(const Dev &D, int code, int where) {
@@ -132,8 +158,8 @@ __device__ __forceinline__ bool wins(int dv, int dw, int v, int w) {
 // pair sums stay within int32, so the packed adds never carry between halves.
 __device__ __forceinline__ void push_res(const Dev &D, int a, int ra, int delta) {
   unsigned long long d64 = (unsigned long long)(unsigned)delta;
-  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[a]), (d64 << 32) - d64);
-  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[ra]), d64 - (d64 << 32));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[MF_SLOT(D, a)]), (d64 << 32) - d64);
+  atomicAdd(reinterpret_cast<unsigned long long *>(&D.rr[MF_SLOT(D, ra)]), d64 - (d64 << 32));
 }
 
 __device__ __forceinline__ int *list_of(const Dev &D, int gen) { return D.list[gen % 3]; }
@@ -188,6 +214,7 @@ struct Snap {
   long long work[3];
   int gr_req[2];
   int due_any[3];
+  int ph2_started, cut_pending;
 };
 
 struct Shared {
@@ -328,29 +355,29 @@ __device__ __forceinline__ void prefetch_next(const Dev &D, Shared &sh, int kind
   const int nl = sh.lqn[next % 3];
   if (t < nl) {
     const int v = sh.lq[next % 3][t];
-    const int beg = __ldg(&D.row[v]);
-    const int deg = __ldg(&D.row[v + 1]) - beg;
+    const int beg = __ldg(&D.row[MF_ROW(D, v)]);
+    const int deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
     if (deg > KT) return;
     int h[KT];
 #pragma unroll
-    for (int i = 0; i < KT; i++) h[i] = i < deg ? __ldg(&D.head[beg + i]) : 0;
+    for (int i = 0; i < KT; i++) h[i] = i < deg ? __ldg(&D.head[MF_SLOT(D, beg + i)]) : 0;
     if (deg > 0) {
-      prefetch_l2(&D.rr[beg]);
-      prefetch_l2(&D.rr[beg + deg - 1]);
+      prefetch_l2(&D.rr[MF_SLOT(D, beg)]);
+      prefetch_l2(&D.rr[MF_SLOT(D, beg + deg - 1)]);
     }
     if (kind == PF_ROUND) {
-      prefetch_l2(&D.vs[v]);
+      prefetch_l2(&D.vs[MF_VTX(D, v)]);
       if (deg > 0) {
-        prefetch_l2(&D.rev[beg]);
-        prefetch_l2(&D.rev[beg + deg - 1]);
+        prefetch_l2(&D.rev[MF_SLOT(D, beg)]);
+        prefetch_l2(&D.rev[MF_SLOT(D, beg + deg - 1)]);
       }
 #pragma unroll
       for (int i = 0; i < KT; i++)
-        if (i < deg) prefetch_l2(&D.vs[h[i]]);
+        if (i < deg) prefetch_l2(&D.vs[MF_VTX(D, h[i])]);
     } else {
 #pragma unroll
       for (int i = 0; i < KT; i++)
-        if (i < deg) prefetch_l2(&D.blab[h[i]]);
+        if (i < deg) prefetch_l2(&D.blab[MF_VTX(D, h[i])]);
     }
 #pragma unroll
     for (int i = 0; i < KT; i++) sh.phead[i][t] = h[i];
@@ -358,7 +385,7 @@ __device__ __forceinline__ void prefetch_next(const Dev &D, Shared &sh, int kind
     sh.pdeg[t] = deg;
     sh.pv[t] = v;
   } else if (kind == PF_ROUND && prev >= 0 && t - nl < sh.lqn[prev % 3]) {
-    prefetch_l2(&D.vs[sh.lq[prev % 3][t - nl]]);
+    prefetch_l2(&D.vs[MF_VTX(D, sh.lq[prev % 3][t - nl])]);
   }
 }
 
@@ -396,6 +423,7 @@ static __device__ bool grid_sync(const Dev &D, Shared &sh, int where, int pf = P
     const long long w0 = __ldcg(&cw->work[0]), w1 = __ldcg(&cw->work[1]), w2 = __ldcg(&cw->work[2]);
     const int2 q = __ldcg(reinterpret_cast<const int2 *>(cw->gr_req));
     const int d0 = vol_read(&cw->due_any[0]), d1 = vol_read(&cw->due_any[1]), d2 = vol_read(&cw->due_any[2]);
+    const int p2 = vol_read(&cw->ph2_started), cp = vol_read(&cw->cut_pending);
     sh.snap.err = err;
     sh.snap.cnt[0] = k.x;
     sh.snap.cnt[1] = k.y;
@@ -413,6 +441,8 @@ static __device__ bool grid_sync(const Dev &D, Shared &sh, int where, int pf = P
     sh.snap.due_any[0] = d0;
     sh.snap.due_any[1] = d1;
     sh.snap.due_any[2] = d2;
+    sh.snap.ph2_started = p2;
+    sh.snap.cut_pending = cp;
   }
   __syncthreads();
   return sh.snap.err == 0;
@@ -626,7 +656,8 @@ __device__ __forceinline__ double inst_progress(const Dev &D, int k, int rnd) {
 // D.carry, and the merge step of the previous round is done now for their
 // vertices (the relabel rebuilds the flagged instances, whose lists the BFS
 // overwrites). Two grid barriers.
-static __device__ bool partial_prep(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, int epoch, int rnd) {
+static __device__ __noinline__ bool partial_prep(const Dev &D, Shared &sh, int r, int gen, bool prev_valid, int epoch,
+                                                 int rnd) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   for (int k = tid; k < D.ninst; k += nthr)
     if (__ldcg(&D.inst[k].due) ||
@@ -739,8 +770,8 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
       dw[i] = 0;
       rv[i] = 0;
       if (i < deg) {
-        rs[i] = __ldcg(&D.rr[beg + i]).x;
-        rv[i] = __ldg(&D.rev[beg + i]);
+        rs[i] = __ldcg(&D.rr[MF_SLOT(D, beg + i)]).x;
+        rv[i] = __ldg(&D.rev[MF_SLOT(D, beg + i)]);
         const int2 x = load_slot(D, R.p, wv[i]);
         dw[i] = x.x;
         if (x.y == R.r) act |= 1u << i;
@@ -764,9 +795,9 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
       dw[i] = 0;
       rv[i] = 0;
       if (i < deg) {
-        wv[i] = __ldg(&D.head[beg + i]);
-        rs[i] = __ldcg(&D.rr[beg + i]).x;
-        rv[i] = __ldg(&D.rev[beg + i]);
+        wv[i] = __ldg(&D.head[MF_SLOT(D, beg + i)]);
+        rs[i] = __ldcg(&D.rr[MF_SLOT(D, beg + i)]).x;
+        rv[i] = __ldg(&D.rev[MF_SLOT(D, beg + i)]);
       }
     }
 #pragma unroll
@@ -842,8 +873,8 @@ __device__ __forceinline__ void discharge_thread(const Dev &D, Shared &sh, const
 static __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
                                long long &work) {
   const int lane = threadIdx.x & 31;
-  const int beg = __ldg(&D.row[v]);
-  const int deg = __ldg(&D.row[v + 1]) - beg;
+  const int beg = __ldg(&D.row[MF_ROW(D, v)]);
+  const int deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
   long long ex = 0;
   if (lane == 0) ex = __ldcg(exc_ptr(D, v)) + (D.simple ? 0 : take_added(D, v));
   ex = __shfl_sync(FULL, ex, 0);
@@ -858,8 +889,8 @@ static __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &
       int w = 0, rs = 0, dw = 0;
       bool wact = false;
       if (i < deg) {
-        w = __ldg(&D.head[beg + i]);
-        rs = __ldcg(&D.rr[beg + i]).x;
+        w = __ldg(&D.head[MF_SLOT(D, beg + i)]);
+        rs = __ldcg(&D.rr[MF_SLOT(D, beg + i)]).x;
         if (rs > 0) {
           const int2 x = load_slot(D, R.p, w);
           dw = x.x;
@@ -880,7 +911,7 @@ static __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &
       st.scans_res += (resid ? 1 : 0);
       bool found = false;
       if (delta > 0) {
-        push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+        push_res(D, beg + i, __ldg(&D.rev[MF_SLOT(D, beg + i)]), (int)delta);
         rs -= (int)delta;
         st.pushes++;
         if (dw == 0) {
@@ -919,8 +950,8 @@ static __device__ void discharge_warp(const Dev &D, Shared &sh, const RoundCtx &
 static __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, int dv, int cap_v, TStat &st,
                                 long long &work, Shared &sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int beg = __ldg(&D.row[v]);
-  const int deg = __ldg(&D.row[v + 1]) - beg;
+  const int beg = __ldg(&D.row[MF_ROW(D, v)]);
+  const int deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
   __syncthreads();
   if (threadIdx.x == 0) sh.lsum[0] = __ldcg(exc_ptr(D, v)) + (D.simple ? 0 : take_added(D, v));
   __syncthreads();
@@ -936,8 +967,8 @@ static __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, i
       int w = 0, rs = 0, dw = 0;
       bool wact = false;
       if (i < deg) {
-        w = __ldg(&D.head[beg + i]);
-        rs = __ldcg(&D.rr[beg + i]).x;
+        w = __ldg(&D.head[MF_SLOT(D, beg + i)]);
+        rs = __ldcg(&D.rr[MF_SLOT(D, beg + i)]).x;
         if (rs > 0) {
           const int2 x = load_slot(D, R.p, w);
           dw = x.x;
@@ -967,7 +998,7 @@ static __device__ void discharge_block(const Dev &D, const RoundCtx &R, int v, i
       st.scans_res += (resid ? 1 : 0);
       bool found = false;
       if (delta > 0) {
-        push_res(D, beg + i, __ldg(&D.rev[beg + i]), (int)delta);
+        push_res(D, beg + i, __ldg(&D.rev[MF_SLOT(D, beg + i)]), (int)delta);
         rs -= (int)delta;
         st.pushes++;
         if (dw == 0) {
@@ -1054,8 +1085,8 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
         v = -1;
       } else {
         k = vi.y;
-        beg = __ldg(&D.row[v]);
-        deg = __ldg(&D.row[v + 1]) - beg;
+        beg = __ldg(&D.row[MF_ROW(D, v)]);
+        deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
         cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
         st.visits_dis++;
       }
@@ -1156,8 +1187,8 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
         *lab_ptr(D, v, R.p ^ 1) = dv;
         v = -1;
       } else {
-        beg = __ldg(&D.row[v]);
-        deg = __ldg(&D.row[v + 1]) - beg;
+        beg = __ldg(&D.row[MF_ROW(D, v)]);
+        deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
         cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
       }
     }
@@ -1175,13 +1206,13 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       }
       __syncthreads();
       const int bv = sh.imin[0];
-      const int b = __ldg(&D.row[bv]), e = __ldg(&D.row[bv + 1]);
+      const int b = __ldg(&D.row[MF_ROW(D, bv)]), e = __ldg(&D.row[MF_ROW(D, bv + 1)]);
       int m = INT_MAX;
       for (int a = b + threadIdx.x; a < e; a += blockDim.x) {
         st.scans_dis++;
-        if (__ldcg(&D.rr[a]).x > 0) {
+        if (__ldcg(&D.rr[MF_SLOT(D, a)]).x > 0) {
           st.scans_res++;
-          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[MF_SLOT(D, a)]), R.p)) + 1);
         }
       }
       m = warp_min(m);
@@ -1197,13 +1228,13 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
       if (!mm) break;
       const int leader = __ffs(mm) - 1;
       const int pv = __shfl_sync(FULL, v, leader);
-      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      const int b = __ldg(&D.row[MF_ROW(D, pv)]), e = __ldg(&D.row[MF_ROW(D, pv + 1)]);
       int m = INT_MAX;
       for (int a = b + lane; a < e; a += 32) {
         st.scans_dis++;
-        if (__ldcg(&D.rr[a]).x > 0) {
+        if (__ldcg(&D.rr[MF_SLOT(D, a)]).x > 0) {
           st.scans_res++;
-          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+          m = min(m, __ldcg(lab_ptr(D, __ldg(&D.head[MF_SLOT(D, a)]), R.p)) + 1);
         }
       }
       m = warp_min(m);
@@ -1215,9 +1246,9 @@ __device__ void relabel_phase(const Dev &D, Shared &sh, int r, int gen, long lon
     if (cls == 1) {
       for (int a = beg; a < beg + deg; a++) {
         st.scans_dis++;
-        if (__ldcg(&D.rr[a]).x > 0) {
+        if (__ldcg(&D.rr[MF_SLOT(D, a)]).x > 0) {
           st.scans_res++;
-          newl = min(newl, __ldcg(lab_ptr(D, __ldg(&D.head[a]), R.p)) + 1);
+          newl = min(newl, __ldcg(lab_ptr(D, __ldg(&D.head[MF_SLOT(D, a)]), R.p)) + 1);
         }
       }
     }
@@ -1266,19 +1297,19 @@ __device__ __forceinline__ unsigned long long bword(int label, unsigned long lon
 
 // Expansion start: clears v's queued bit and returns its label.
 __device__ __forceinline__ int bfs_take(const Dev &D, int v) {
-  return (int)(atomicAnd(D.blab + v, ~BQ) >> 32);
+  return (int)(atomicAnd(D.blab + MF_VTX(D, v), ~BQ) >> 32);
 }
 
 // Offers label l to w; true when w must join the next list.
 __device__ __forceinline__ bool bfs_offer(const Dev &D, int w, int l) {
   const unsigned long long c = bword(l, BQ);
-  const unsigned long long old = atomicMin(D.blab + w, c);
+  const unsigned long long old = atomicMin(D.blab + MF_VTX(D, w), c);
   return old > c && !(old & BQ);
 }
 
 __device__ __forceinline__ void bfs_arc(const Dev &D, Shared &sh, int a, int l, bool reverse, int next) {
-  const int w = __ldg(&D.head[a]);
-  const int2 x = __ldcg(&D.rr[a]);
+  const int w = __ldg(&D.head[MF_SLOT(D, a)]);
+  const int2 x = __ldcg(&D.rr[MF_SLOT(D, a)]);
   const int cf = reverse ? x.y : x.x;
   if (cf > 0 && bfs_offer(D, w, l)) qpush(D, sh, next, w);
 }
@@ -1295,8 +1326,8 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
     w[i] = 0;
     cf[i] = 0;
     if (i < deg) {
-      w[i] = (pre && i < KT) ? sh.phead[i < KT ? i : 0][threadIdx.x] : __ldg(&D.head[beg + i]);
-      const int2 x = __ldcg(&D.rr[beg + i]);
+      w[i] = (pre && i < KT) ? sh.phead[i < KT ? i : 0][threadIdx.x] : __ldg(&D.head[MF_SLOT(D, beg + i)]);
+      const int2 x = __ldcg(&D.rr[MF_SLOT(D, beg + i)]);
       cf[i] = reverse ? x.y : x.x;
     }
   }
@@ -1306,8 +1337,8 @@ __device__ __forceinline__ void bfs_thread(const Dev &D, Shared &sh, int beg, in
 #pragma unroll
     for (int i = 0; i < KTD; i++) {
       got[i] = cf[i] > 0 && bfs_offer(D, w[i], l);
-      rb[i] = cf[i] > 0 ? __ldg(&D.row[w[i]]) : 0;
-      re[i] = cf[i] > 0 ? __ldg(&D.row[w[i] + 1]) : 0;
+      rb[i] = cf[i] > 0 ? __ldg(&D.row[MF_ROW(D, w[i])]) : 0;
+      re[i] = cf[i] > 0 ? __ldg(&D.row[MF_ROW(D, w[i] + 1)]) : 0;
     }
 #pragma unroll
     for (int i = 0; i < KTD; i++)
@@ -1346,8 +1377,8 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
         beg = sh.pbeg[threadIdx.x];
         deg = sh.pdeg[threadIdx.x];
       } else {
-        beg = __ldg(&D.row[v]);
-        deg = __ldg(&D.row[v + 1]) - beg;
+        beg = __ldg(&D.row[MF_ROW(D, v)]);
+        deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
       }
       cls = deg <= KTD ? 1 : (deg <= D.bin_warp ? 2 : 3);
       st.scans_bfs += deg;
@@ -1367,7 +1398,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
       }
       __syncthreads();
       const int pv = sh.imin[0], pl = sh.imin[1];
-      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      const int b = __ldg(&D.row[MF_ROW(D, pv)]), e = __ldg(&D.row[MF_ROW(D, pv + 1)]);
       for (int a = b + threadIdx.x; a < e; a += blockDim.x) bfs_arc(D, sh, a, pl, reverse, next);
       __syncthreads();
     }
@@ -1378,7 +1409,7 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
       const int pv = __shfl_sync(FULL, v, leader);
       const int pl = __shfl_sync(FULL, l, leader);
       if (lane == leader) cls = 0;
-      const int b = __ldg(&D.row[pv]), e = __ldg(&D.row[pv + 1]);
+      const int b = __ldg(&D.row[MF_ROW(D, pv)]), e = __ldg(&D.row[MF_ROW(D, pv + 1)]);
       for (int a = b + lane; a < e; a += 32) bfs_arc(D, sh, a, pl, reverse, next);
       __syncwarp();
     }
@@ -1399,8 +1430,8 @@ __device__ void bfs_level(const Dev &D, Shared &sh, int gen, bool reverse, TStat
     __syncthreads();
     if (v >= 0) {
       if (deg < 0) {
-        beg = __ldg(&D.row[v]);
-        deg = __ldg(&D.row[v + 1]) - beg;
+        beg = __ldg(&D.row[MF_ROW(D, v)]);
+        deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
       }
       if (deg > KT) {
         qpush(D, sh, next, v);  // still queued: the next level's sweep expands it
@@ -1436,22 +1467,22 @@ static __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int dep
     int beg = 0, deg = 0;
     bool open = false;
     if (w >= 0) {
-      const unsigned long long x = __ldcg(D.blab + w);
+      const unsigned long long x = __ldcg(D.blab + MF_VTX(D, w));
       open = (int)(x >> 32) == UNV && !(x & BB);
       if (open) {
-        beg = __ldg(&D.row[w]);
-        deg = __ldg(&D.row[w + 1]) - beg;
+        beg = __ldg(&D.row[MF_ROW(D, w)]);
+        deg = __ldg(&D.row[MF_ROW(D, w + 1)]) - beg;
         open = deg > 0;
       }
     }
     if (open && deg <= 32) {  // thread per vertex, stop at the first arc into the level
       for (int i = 0; i < deg; i++) {
         st.scans_bfs++;
-        const int2 r = __ldcg(&D.rr[beg + i]);
+        const int2 r = __ldcg(&D.rr[MF_SLOT(D, beg + i)]);
         if ((reverse ? r.x : r.y) <= 0) continue;
-        const unsigned long long y = __ldcg(D.blab + __ldg(&D.head[beg + i]));
+        const unsigned long long y = __ldcg(D.blab + MF_VTX(D, __ldg(&D.head[MF_SLOT(D, beg + i)])));
         if ((int)(y >> 32) == depth && !(y & BB)) {
-          D.blab[w] = bword(depth + 1, BQ);
+          D.blab[MF_VTX(D, w)] = bword(depth + 1, BQ);
           st.visits_bfs++;
           qpush(D, sh, next, w);
           break;
@@ -1472,15 +1503,15 @@ static __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int dep
         if (c + lane < pd) {
           st.scans_bfs++;
           const int a = pb + c + lane;
-          const int2 r = __ldcg(&D.rr[a]);
+          const int2 r = __ldcg(&D.rr[MF_SLOT(D, a)]);
           if ((reverse ? r.x : r.y) > 0) {
-            const unsigned long long y = __ldcg(D.blab + __ldg(&D.head[a]));
+            const unsigned long long y = __ldcg(D.blab + MF_VTX(D, __ldg(&D.head[MF_SLOT(D, a)])));
             hit = (int)(y >> 32) == depth && !(y & BB);
           }
         }
         if (__ballot_sync(FULL, hit)) {
           if (lane == 0) {
-            D.blab[pw] = bword(depth + 1, BQ);
+            D.blab[MF_VTX(D, pw)] = bword(depth + 1, BQ);
             st.visits_bfs++;
             qpush(D, sh, next, pw);
           }
@@ -1519,19 +1550,20 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
         qpush(D, sh, next, v);
       }
     }
-    D.blab[v] = x;
+    D.blab[MF_VTX(D, v)] = x;
   });
   phase_end(D, sh, next, 0, nullptr);
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
+  // (seeds and blockers are read through L2: a union's per-instance seeds change during the launch)
   for (int i = tid; i < nterm; i += nthr) {
     if (S.on && __ldcg(&D.live[i]) != S.epoch) continue;
-    D.blab[seeds[i]] = bword(0, BQ);
-    if (blockers) D.blab[blockers[i]] = bword(0, BB);
+    D.blab[MF_VTX(D, __ldcg(&seeds[i]))] = bword(0, BQ);
+    if (blockers) D.blab[MF_VTX(D, __ldcg(&blockers[i]))] = bword(0, BB);
   }
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nterm; i += blockDim.x)
-      if (!S.on || __ldcg(&D.live[i]) == S.epoch) append(D, next, seeds[i]);
+      if (!S.on || __ldcg(&D.live[i]) == S.epoch) append(D, next, __ldcg(&seeds[i]));
   if (!grid_sync(D, sh, where)) return false;
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1586,6 +1618,7 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
         I->last = rnd;
         I->depth = 0;
         I->due = 0;
+        I->act = 0;
       }
   }
   if (!bfs<KTD>(D, sh, sinks, sources, D.ninst, true, false, gen, st, 2, S)) return false;
@@ -1598,11 +1631,12 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
   }
   for_covered(D, S, [&](int v, bool valid) {
     int depth = -1, k = -1;
+    bool active = false;
     if (valid) {
       const int2 vi = vinst_of<MULTI>(D, v);
       const int c = vi.x;
       k = vi.y;
-      const int d = bfs_label(__ldcg(D.blab + v), c);
+      const int d = bfs_label(__ldcg(D.blab + MF_VTX(D, v)), c);
       *lab_ptr(D, v, 0) = d;
       *lab_ptr(D, v, 1) = d;
       const longlong2 ea = load_ea(D, v);
@@ -1616,14 +1650,18 @@ __device__ bool global_relabel(const Dev &D, Shared &sh, const int *sinks, const
       if (d > 0 && d < c && ev > 0) {
         *act_ptr(D, v, p) = r;
         qpush(D, sh, next, v);
+        active = true;
       }
       if (d < c) depth = d;
     }
-    if (MULTI && D.inst_relabel) {  // depth of every covered instance: its largest finite label
+    if (MULTI && D.inst_relabel) {  // every covered instance: its depth (largest finite label), its active vertices
       const int kk = depth >= 0 ? k : -1;
       const unsigned grp = __match_any_sync(FULL, kk);
       const int dmax = __reduce_max_sync(grp, depth);
       if (kk >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&D.inst[kk].depth, dmax);
+      const int ka = active ? k : -1;
+      const unsigned ga = __match_any_sync(FULL, ka);
+      if (ka >= 0 && (threadIdx.x & 31) == __ffs(ga) - 1) atomicAdd(&D.inst[ka].act, __popc(ga));
     }
   });
   if (carried) {  // working-set entries of the instances this relabel did not cover (partial_prep)
@@ -1798,6 +1836,232 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
   return true;
 }
 
+// ------------------------------------------------------------------ unions
+//
+// Batches and service unions with per-instance relabel schedules: every
+// instance goes through its own phases inside the one launch, as it would
+// solved alone: the preflow (rounds toward its t), the flow phase (its excess
+// back to its s), then its cut BFS and its outputs, after which its results
+// are final (and, with D.done_flag, announced to the host while the others
+// go on). An instance's phase ends when a global relabel covering it finds no
+// active vertex of it, as a phase of a single graph ends (reading 9). Every
+// global relabel here covers a set of flagged instances (partial_prep): the
+// ones that asked for one, or every instance not done yet when the working
+// set is empty, and carries the working sets of the others over.
+
+// Instance k's value is final once its preflow ended: the excess of its sink.
+// Transitions after a relabel that covered the instances flagged `epoch`: one
+// without active vertices ends its phase (preflow: value recorded, next relabel
+// from s, blocking t; flow: cut pending). Ends with a grid barrier.
+static __device__ __noinline__ bool union_transitions(const Dev &D, Shared &sh, int epoch, int gen) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  if (tid == 0) {
+    D.ctl->ph2_started = 0;
+    D.ctl->cut_pending = 0;
+  }
+  if (!grid_sync(D, sh, 3)) return false;
+  for (int k = tid; k < D.ninst; k += nthr) {
+    if (__ldcg(&D.live[k]) != epoch) continue;
+    InstState *I = D.inst + k;
+    if (__ldcg(&I->act) != 0) continue;
+    const int ph = __ldcg(&I->ph);
+    if (ph == 1) {
+      const long long val = __ldcg(exc_ptr(D, D.snk[k]));
+      if (D.out_value) D.out_value[k] = val;
+      if (k == 0) D.ctl->value = val;
+      I->ph = 2;
+      D.gseed[k] = D.src[k];
+      D.gblock[k] = D.snk[k];
+      I->due = 1;
+      D.ctl->ph2_started = 1;
+    } else if (ph == 2) {
+      I->ph = 3;
+      D.ctl->cut_pending = 1;
+    }
+  }
+  return grid_sync(D, sh, 3, PF_ROUND, gen);
+}
+
+// Cut and outputs of the instances whose flow phase ended (phase 3): BFS from
+// their sources over residual arcs (S_min), their cut bitmaps (word-aligned per
+// instance), their per-slot flows, a check that none of their vertices other
+// than s and t kept excess, then phase 4 and the host's flag. Runs right after
+// a global relabel; the working set of the other instances (list generation
+// gen, which the BFS's lists overwrite) is saved in D.carry and comes back as
+// the next generation, stamps unchanged.
+template <int KTD>
+__device__ __noinline__ bool union_cut(const Dev &D, Shared &sh, int &gen, TStat &st, int &epoch) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const Sel S{true, ++epoch};
+  for (int k = tid; k < D.ninst; k += nthr)
+    if (__ldcg(&D.inst[k].ph) == 3) D.live[k] = S.epoch;
+  if (tid == 0) D.ctl->carry_n = 0;
+  if (!grid_sync(D, sh, 9)) return false;
+  {
+    const int cnt = list_count(D, sh, gen);
+    const int *L = list_of(D, gen);
+    for (int i = tid; i < cnt; i += nthr) carry_push(D, __ldcg(&L[i]));
+    const int *lq = sh.lq[gen % 3];
+    for (int i = threadIdx.x; i < sh.lqn[gen % 3]; i += blockDim.x) carry_push(D, lq[i]);
+  }
+  if (!grid_sync(D, sh, 9)) return false;
+  if (!bfs<KTD>(D, sh, D.src, nullptr, D.ninst, false, false, gen, st, 9, S)) return false;
+  long long left = 0;
+  for (int t = blockIdx.x; t < D.ntiles; t += gridDim.x) {
+    const int4 T = __ldg(&D.tiles[t]);
+    if (__ldcg(&D.live[T.z]) != S.epoch) continue;  // uniform in the CTA
+    const int k = T.z, V = __ldg(&D.voff[k]);
+    if (D.out_cutw) {  // bit v of instance k at bit (v - V) of its run; tiles start at multiples of 32 in it
+      const int words = (T.y - T.x + 31) >> 5;
+      unsigned *out = D.out_cutw + D.cwoff[k] + ((T.x - V) >> 5);
+      for (int w = threadIdx.x; w < words; w += blockDim.x) {
+        unsigned bits = 0;
+        for (int j = 0; j < 32; j++) {
+          const int v = T.x + 32 * w + j;
+          if (v < T.y && (int)(__ldcg(D.blab + MF_VTX(D, v)) >> 32) != UNV) bits |= 1u << j;
+        }
+        out[w] = bits;
+      }
+    }
+    if (D.out_flow) {
+      const int a0 = __ldg(&D.row[MF_ROW(D, T.x)]), a1 = __ldg(&D.row[MF_ROW(D, T.y)]);
+      for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        const int f = __ldg(&D.cap[MF_SLOT(D, a)]) - __ldcg(&D.rr[MF_SLOT(D, a)]).x;
+        D.out_flow[a] = f > 0 ? f : 0;
+      }
+    }
+    for (int v = T.x + threadIdx.x; v < T.y; v += blockDim.x)
+      if (v != D.src[k] && v != D.snk[k] && __ldcg(exc_ptr(D, v)) != 0) left++;
+  }
+  left = block_sum(left, sh);
+  if (threadIdx.x == 0 && left) {
+    atomic_add64(&D.ctl->leftover, left);
+    set_err(D, MF_ERR_INTERNAL, 8);
+  }
+  {  // the saved working set becomes the next generation (the BFS left generation gen empty)
+    const int next = gen + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      D.ctl->cnt[(gen + 2) & 3] = 0;
+      D.ctl->lcnt[(gen + 2) & 3] = 0;
+    }
+    const int cn = min(__ldcg(&D.ctl->carry_n), D.n);
+    for (int i = tid; i < cn; i += nthr) qpush(D, sh, next, __ldcg(&D.carry[i]));
+    phase_end(D, sh, next, 0, nullptr);
+  }
+  if (!grid_sync(D, sh, 9)) return false;
+  gen++;
+  for (int k = tid; k < D.ninst; k += nthr) {
+    if (__ldcg(&D.live[k]) != S.epoch) continue;
+    D.inst[k].ph = 4;
+    atomicAdd(&D.ctl->done_cnt, 1);
+    if (D.done_flag) {
+      __threadfence_system();  // the outputs before the flag, for the host and its copies
+      D.done_flag[k] = 1u;
+    }
+  }
+  return grid_sync(D, sh, 9, PF_ROUND, gen);
+}
+
+// Instances whose working set ran empty without a relabel of theirs (between
+// rounds; the next round has index rnd and working set generation gen): flag
+// the instances present in the working set; every other instance not finished
+// asks for a relabel, under the request flag of the round just finished.
+static __device__ __noinline__ bool union_presence(const Dev &D, Shared &sh, int gen, int rnd) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int cnt = list_count(D, sh, gen);
+  const int *L = list_of(D, gen);
+  const int mark = -2 - rnd;  // never a relabel epoch (those are positive)
+  for (int i = tid; i < cnt; i += nthr) D.live[__ldg(&D.vinst[__ldcg(&L[i])]).y] = mark;
+  for (int i = threadIdx.x; i < sh.lqn[gen % 3]; i += blockDim.x) D.live[__ldg(&D.vinst[sh.lq[gen % 3][i]]).y] = mark;
+  if (!grid_sync(D, sh, 4)) return false;
+  for (int k = tid; k < D.ninst; k += nthr) {
+    InstState *I = D.inst + k;
+    const int ph = __ldcg(&I->ph);
+    if ((ph == 1 || ph == 2) && __ldcg(&D.live[k]) != mark && !__ldcg(&I->due)) {
+      I->due = 1;
+      D.ctl->due_any[(rnd + 2) % 3] = 1;  // read at the next barrier
+    }
+  }
+  return grid_sync(D, sh, 4, PF_ROUND, gen);
+}
+
+// The whole solve of a union with per-instance phases (see above).
+template <int KTD>
+__device__ bool run_union(const Dev &D, Shared &sh, int &r, int &gen, long long &rnd, TStat &st, int &epoch) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  bool fresh = false, prev_valid = false, full_next = true, pending = false;
+  long long rounds = 0;
+  unsigned long long last_gr_end = 0;  // CTA 0 thread 0
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  for (;;) {
+    // instances whose working set ran empty without a relabel of theirs: every 16 rounds, flag the
+    // instances present in the working set; the others, not finished, ask for a relabel
+    if (!fresh && rounds > 0 && rounds % 16 == 0 && !full_next && !pending && !union_presence(D, sh, gen, (int)rnd))
+      return false;
+    const bool partial = !full_next && (pending || (!fresh && sh.snap.due_any[(rnd + 2) % 3] != 0));
+    if (full_next || partial) {
+      const unsigned long long t0 = timer ? gtimer() : 0;
+      const int ep = ++epoch;
+      if (timer && partial) D.ctl->grs_partial++;
+      if (full_next)  // cover every instance not finished: flag them as asking
+        for (int k = tid; k < D.ninst; k += nthr)
+          if (__ldcg(&D.inst[k].ph) <= 2) D.inst[k].due = 1;
+      if (full_next && !grid_sync(D, sh, 2)) return false;
+      if (!partial_prep(D, sh, r, gen, prev_valid, ep, (int)rnd)) return false;
+      r += 2;  // fresh stamps, same label slot for the carried entries
+      if (!global_relabel<KTD, true>(D, sh, D.gseed, D.gblock, r, gen, st, Sel{true, ep}, (int)rnd, true))
+        return false;
+      if (!union_transitions(D, sh, ep, gen)) return false;
+      if (sh.snap.cut_pending && !union_cut<KTD>(D, sh, gen, st, epoch)) return false;
+      pending = sh.snap.ph2_started != 0;
+      if (timer) {
+        last_gr_end = gtimer();
+        D.ctl->t_gr += last_gr_end - t0;
+      }
+      full_next = false;
+      fresh = true;
+      prev_valid = false;
+    }
+    const long long count = gen_total(D, sh, gen);
+    if (count == 0) {
+      if (vol_read(&D.ctl->done_cnt) >= D.ninst) break;  // every CTA reads the same: written before a barrier
+      if (!pending) full_next = true;  // confirm the instances not finished (or start their next phase)
+      fresh = false;
+      continue;
+    }
+    if (rounds >= 2 * D.max_rounds) {
+      set_err(D, MF_ERR_ITER_LIMIT, 10);
+      return false;
+    }
+    unsigned long long t0 = 0;
+    if (timer) {
+      D.ctl->rounds_by_size[count < 1024 ? 0 : count < 16384 ? 1 : count < 262144 ? 2 : 3]++;
+      if (D.trace && rnd < D.trace_cap) D.trace[rnd] = make_int2((int)count, fresh ? 1 : 0);
+      t0 = gtimer();
+    }
+    fresh = false;
+    unsigned long long tp = t0;
+    round_phase<KTD, true>(D, sh, r, gen, prev_valid, rnd, st, tp);
+    if (!grid_sync(D, sh, 4, D.simple ? PF_NONE : PF_ROUND, gen + 1, gen)) return false;
+    if (D.simple) {
+      relabel_phase<true>(D, sh, r, gen, rnd, st);
+      if (!grid_sync(D, sh, 4)) return false;
+    }
+    if (timer) {
+      const unsigned long long t3 = gtimer();
+      D.ctl->t_dis += t3 - t0;
+      D.ctl->t_rwait += t3 - tp;
+    }
+    r++;
+    gen++;
+    rnd++;
+    rounds++;
+    prev_valid = true;
+    if (timer) D.ctl->rounds++;
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int KTD, bool MULTI>
@@ -1817,10 +2081,10 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
 
   // Initialisation (Algorithm 1): residuals from the capacities, labels 0,
   // excess 0, no stamps.
-  for (int a = tid; a < D.m; a += nthr) D.rr[a] = make_int2(__ldg(&D.cap[a]), __ldg(&D.cap[__ldg(&D.rev[a])]));
+  for (int a = tid; a < D.m; a += nthr) D.rr[MF_SLOT(D, a)] = make_int2(__ldg(&D.cap[MF_SLOT(D, a)]), __ldg(&D.cap[MF_SLOT(D, __ldg(&D.rev[MF_SLOT(D, a)]))]));
   for (int v = tid; v < D.n; v += nthr) {
-    reinterpret_cast<int4 *>(D.vs + v)[0] = make_int4(0, -1, 0, -1);
-    reinterpret_cast<longlong2 *>(D.vs + v)[1] = make_longlong2(0, 0);
+    reinterpret_cast<int4 *>(D.vs + MF_VTX(D, v))[0] = make_int4(0, -1, 0, -1);
+    reinterpret_cast<longlong2 *>(D.vs + MF_VTX(D, v))[1] = make_longlong2(0, 0);
   }
   if (D.gap_every > 0)
     for (int k = tid; k <= D.n_cap; k += nthr) D.hist[k] = 0;
@@ -1830,23 +2094,27 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
     for (int k = tid; k < D.ninst; k += nthr) {
       const double thr = (D.gr_alpha * (double)(__ldg(&D.voff[k + 1]) - __ldg(&D.voff[k])) +
                           (double)__ldg(&D.inst_marcs[k])) / D.gr_freq;
-      D.inst[k] = InstState{thr > 9.0e18 ? (long long)9e18 : (long long)thr, 0, 0, 0, {0, 0, 0}};
+      D.inst[k] = InstState{thr > 9.0e18 ? (long long)9e18 : (long long)thr, 0, 0, 0, 1, 0, 0};
       D.inst_work[(size_t)k * INST_WORK_STRIDE] = 0;
+      if (D.gseed) {
+        D.gseed[k] = D.snk[k];
+        D.gblock[k] = D.src[k];
+      }
     }
   bool ok = grid_sync(D, sh, 0);
   // Saturate every arc out of each source (self-loops excluded).
   if (ok) {
     for (int k = 0; k < D.ninst; k++) {
       const int s = D.src[k];
-      const int b = __ldg(&D.row[s]), e = __ldg(&D.row[s + 1]);
+      const int b = __ldg(&D.row[MF_ROW(D, s)]), e = __ldg(&D.row[MF_ROW(D, s + 1)]);
       for (int a = b + tid; a < e; a += nthr) {
-        const int c = __ldg(&D.cap[a]);
-        const int w = __ldg(&D.head[a]);
+        const int c = __ldg(&D.cap[MF_SLOT(D, a)]);
+        const int w = __ldg(&D.head[MF_SLOT(D, a)]);
         if (c <= 0 || w == s) continue;
-        const int ra = __ldg(&D.rev[a]);
-        const int cr = __ldg(&D.cap[ra]);
-        D.rr[a] = make_int2(0, cr + c);
-        D.rr[ra] = make_int2(cr + c, 0);
+        const int ra = __ldg(&D.rev[MF_SLOT(D, a)]);
+        const int cr = __ldg(&D.cap[MF_SLOT(D, ra)]);
+        D.rr[MF_SLOT(D, a)] = make_int2(0, cr + c);
+        D.rr[MF_SLOT(D, ra)] = make_int2(cr + c, 0);
         atomic_add64(exc_ptr(D, w), c);
       }
     }
@@ -1854,8 +2122,14 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
   }
   int r = 0, gen = 0, epoch = 0;
   long long rnd = 0;
-  if (ok) ok = run_phase<KTD, MULTI>(D, sh, D.snk, D.src, r, gen, rnd, true, st, epoch);
-  if (ok && D.mode == MODE_SOLVE) {
+  // unions with per-instance schedules: every instance's phases, cut and outputs inside run_union
+  const bool per_instance = MULTI && D.union_phases && D.inst_relabel && D.mode == MODE_SOLVE && !D.cut_only && D.gseed;
+  if (ok && per_instance) {
+    ok = run_union<KTD>(D, sh, r, gen, rnd, st, epoch);
+    if (tid == 0) D.ctl->t_preflow = gtimer();
+  }
+  if (!per_instance && ok) ok = run_phase<KTD, MULTI>(D, sh, D.snk, D.src, r, gen, rnd, true, st, epoch);
+  if (!per_instance && ok && D.mode == MODE_SOLVE) {
     if (tid == 0) D.ctl->t_preflow = gtimer();
     for (int k = tid; k < D.ninst; k += nthr) {
       const long long val = __ldcg(exc_ptr(D, D.snk[k]));
@@ -1892,14 +2166,14 @@ __device__ __forceinline__ void solve_body(const Dev &D) {
           unsigned bits = 0;
           for (int j = 0; j < 32; j++) {
             const int v = wd * 32 + j;
-            if (v < D.n && (int)(__ldcg(D.blab + v) >> 32) != UNV) bits |= 1u << j;
+            if (v < D.n && (int)(__ldcg(D.blab + MF_VTX(D, v)) >> 32) != UNV) bits |= 1u << j;
           }
           D.out_cut[wd] = bits;
         }
       }
       if (D.out_flow)
         for (int a = tid; a < D.m; a += nthr) {
-          const int f = __ldg(&D.cap[a]) - __ldcg(&D.rr[a]).x;
+          const int f = __ldg(&D.cap[MF_SLOT(D, a)]) - __ldcg(&D.rr[MF_SLOT(D, a)]).x;
           D.out_flow[a] = f > 0 ? f : 0;
         }
     }

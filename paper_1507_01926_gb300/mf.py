@@ -81,6 +81,16 @@ EXPORTS = ["mf_default_options", "mf_struct_sizes", "mf_last_error", "mf_build_c
            "mf_set_options", "mf_autotune", "mf_batch_set_options", "mf_batch_autotune"]
 
 
+def use_library(path: str | None):
+    """Makes every later call of this module go to the library at `path` (None: back to libmf.so); used by the
+    tests of the build with checked gathers (libmf_check.so). Returns the path in use before."""
+    global _lib, LIB_PATH
+    before = LIB_PATH
+    LIB_PATH = path or os.path.join(_HERE, "libmf.so")
+    _lib = None
+    return before
+
+
 def lib():
     """Loads libmf.so (raises OSError if it is missing or cannot be loaded)."""
     global _lib
