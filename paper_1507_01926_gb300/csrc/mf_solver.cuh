@@ -1077,6 +1077,8 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
       cls = 4;
     } else if (kind == 1) {
       v = x;
+      // label and row offsets in one round trip (the offsets are unused when the label is at the cap)
+      const int b0 = __ldg(&D.row[MF_ROW(D, v)]), b1 = __ldg(&D.row[MF_ROW(D, v + 1)]);
       dv = __ldcg(lab_ptr(D, v, R.p));
       const int2 vi = vinst_of<MULTI>(D, v);
       cap_v = vi.x;
@@ -1085,8 +1087,8 @@ __device__ void round_phase(const Dev &D, Shared &sh, int r, int gen, bool prev_
         v = -1;
       } else {
         k = vi.y;
-        beg = __ldg(&D.row[MF_ROW(D, v)]);
-        deg = __ldg(&D.row[MF_ROW(D, v + 1)]) - beg;
+        beg = b0;
+        deg = b1 - b0;
         cls = deg <= D.bin_thread ? 1 : (deg <= D.bin_warp ? 2 : 3);
         st.visits_dis++;
       }
@@ -1524,6 +1526,37 @@ static __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int dep
   phase_end(D, sh, next, 0, nullptr);
 }
 
+// Level 0 of a BFS from one seed with many arcs (slots [b, e)), the seed
+// labelled 0 and not queued (generation gen is empty): the whole grid offers
+// label 1 along its arcs, one arc per thread, into generation gen + 1. Ends
+// with a grid barrier.
+static __device__ __noinline__ bool bfs_wide_level(const Dev &D, Shared &sh, int gen, int b, int e, bool reverse,
+                                                   TStat &st, int where) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const unsigned long long t0 = timer ? gtimer() : 0;
+  if (timer) {
+    D.ctl->cnt[(gen + 2) & 3] = 0;
+    D.ctl->lcnt[(gen + 2) & 3] = 0;
+    const long long k = D.ctl->levels;
+    if (D.trace_lv && k < D.trace_lv_cap) D.trace_lv[k] = 1;
+    st.visits_bfs++;
+  }
+  for (int a = b + tid; a < e; a += nthr) {
+    bfs_arc(D, sh, a, 1, reverse, gen + 1);
+    st.scans_bfs++;
+  }
+  phase_end(D, sh, gen + 1, 0, nullptr);
+  const unsigned long long t1 = timer ? gtimer() : 0;
+  if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
+  if (timer) {
+    D.ctl->levels++;
+    D.ctl->t_lwork += t1 - t0;
+    D.ctl->t_lwait += gtimer() - t1;
+  }
+  return true;
+}
+
 // BFS from `seeds` (label 0) over blab. `blockers` are never entered. With
 // `excess_seeds`, every vertex holding excess whose label lies in [1, cap] is
 // a seed as well (cut from the maximum preflow). Returns false on error. On
@@ -1556,18 +1589,36 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
   if (!grid_sync(D, sh, where)) return false;
   // phase B: terminals (seeds join generation gen + 1 as well)
   // (seeds and blockers are read through L2: a union's per-instance seeds change during the launch)
+  // A lone seed with more arcs than a CTA has threads (the sink or the source of a single graph) is not
+  // queued: its level is expanded below by the whole grid, one arc per thread, instead of by one CTA.
+  int wide_b = 0, wide_e = 0;
+  if (nterm == 1 && !excess_seeds && !S.on) {
+    const int s0 = __ldcg(&seeds[0]);
+    const int b = __ldg(&D.row[MF_ROW(D, s0)]), e = __ldg(&D.row[MF_ROW(D, s0 + 1)]);
+    if (e - b > (int)blockDim.x) {
+      wide_b = b;
+      wide_e = e;
+    }
+  }
+  const bool wide = wide_e > wide_b;  // the same in every thread
   for (int i = tid; i < nterm; i += nthr) {
     if (S.on && __ldcg(&D.live[i]) != S.epoch) continue;
-    D.blab[MF_VTX(D, __ldcg(&seeds[i]))] = bword(0, BQ);
+    D.blab[MF_VTX(D, __ldcg(&seeds[i]))] = bword(0, wide ? 0 : BQ);
     if (blockers) D.blab[MF_VTX(D, __ldcg(&blockers[i]))] = bword(0, BB);
   }
-  if (blockIdx.x == 0)
+  if (blockIdx.x == 0 && !wide)
     for (int i = threadIdx.x; i < nterm; i += blockDim.x)
       if (!S.on || __ldcg(&D.live[i]) == S.epoch) append(D, next, __ldcg(&seeds[i]));
   if (!grid_sync(D, sh, where)) return false;
   gen++;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-  for (int depth = 0;; depth++) {
+  int depth0 = 0;
+  if (wide) {
+    if (!bfs_wide_level(D, sh, gen, wide_b, wide_e, reverse, st, where)) return false;
+    gen++;
+    depth0 = 1;
+  }
+  for (int depth = depth0;; depth++) {
     const long long fcount = gen_total(D, sh, gen);
     if (fcount == 0) break;
     if (timer && D.trace_lv) {
