@@ -278,11 +278,16 @@ int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d
  * first `capacity` push-relabel rounds of both phases, the working-set size
  * (live[k]) and whether a global relabel ran right before the round
  * (relabel_before[k] = 1), and for each of the first `level_capacity` BFS
- * levels its frontier size (level_sizes[k]). *rounds and *levels (nullable)
- * = totals (may exceed the capacities). Host arrays, nullable when their
- * capacity is 0. */
+ * levels (grid barriers of a BFS: Algorithm 2 and the cut) its frontier size
+ * (level_sizes[k]). round_ns[k] and level_ns[k] (nullable; same capacities)
+ * receive the duration of round / level k in ns as CTA 0 sees it, from its
+ * start to the end of the grid barrier that closes it (%globaltimer; clipped
+ * to INT32_MAX), so that the time of a solve can be split by working-set
+ * size. *rounds and *levels (nullable) = totals (may exceed the capacities).
+ * Host arrays, nullable when their capacity is 0. */
 int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds,
-                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels);
+                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels, int32_t *round_ns,
+                   int32_t *level_ns);
 
 /* Counters of the last solve on g. */
 int mf_get_stats(const mf_graph *g, mf_stats *out);

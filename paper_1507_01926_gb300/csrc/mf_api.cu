@@ -668,7 +668,8 @@ int mf_solve_device(mf_graph *g, void *stream, int64_t *d_flow_value, int32_t *d
 }
 
 int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t capacity, int64_t *rounds,
-                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels) {
+                   int32_t *level_sizes, int64_t level_capacity, int64_t *levels, int32_t *round_ns,
+                   int32_t *level_ns) {
   clear_error();
   if (!g || capacity < 0 || (capacity > 0 && (!live || !relabel_before)) || level_capacity < 0 ||
       (level_capacity > 0 && !level_sizes))
@@ -676,27 +677,37 @@ int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t 
   cudaError_t e = cudaSetDevice(g->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   int2 *tr = nullptr;
-  int *tl = nullptr;
-  if (capacity > 0 && (e = cudaMalloc((void **)&tr, (size_t)capacity * sizeof(int2))) != cudaSuccess)
-    return cuda_fail(e, "cudaMalloc trace");
-  if (level_capacity > 0 && (e = cudaMalloc((void **)&tl, (size_t)level_capacity * sizeof(int))) != cudaSuccess) {
+  int *trn = nullptr, *tl = nullptr, *tln = nullptr;
+  auto release = [&]() {
     if (tr) cudaFree(tr);
+    if (trn) cudaFree(trn);
+    if (tl) cudaFree(tl);
+    if (tln) cudaFree(tln);
+  };
+  if ((capacity > 0 && (e = cudaMalloc((void **)&tr, (size_t)capacity * sizeof(int2))) != cudaSuccess) ||
+      (capacity > 0 && round_ns && (e = cudaMalloc((void **)&trn, (size_t)capacity * sizeof(int))) != cudaSuccess) ||
+      (level_capacity > 0 && (e = cudaMalloc((void **)&tl, (size_t)level_capacity * sizeof(int))) != cudaSuccess) ||
+      (level_capacity > 0 && level_ns &&
+       (e = cudaMalloc((void **)&tln, (size_t)level_capacity * sizeof(int))) != cudaSuccess)) {
+    release();
     return cuda_fail(e, "cudaMalloc trace");
   }
   Dev D = make_dev(g);
   D.out_value = g->d_value;
   D.trace = tr;
+  D.trace_ns = trn;
   D.trace_cap = capacity;
   D.trace_lv = tl;
+  D.trace_lv_ns = tln;
   D.trace_lv_cap = level_capacity;
   int rc = run_kernel(g, D, g->stream);
   if (rc == MF_OK && level_capacity > 0) {
     const long long nl = g->h_ctl->levels < level_capacity ? g->h_ctl->levels : level_capacity;
     e = cudaMemcpy(level_sizes, tl, (size_t)nl * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && tln) e = cudaMemcpy(level_ns, tln, (size_t)nl * sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "trace copy");
   }
   if (levels && rc == MF_OK) *levels = g->h_ctl->levels;
-  if (tl) cudaFree(tl);
   if (rc == MF_OK && capacity > 0) {
     const long long nr = g->h_ctl->rounds < capacity ? g->h_ctl->rounds : capacity;
     int2 *h = (int2 *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int2));
@@ -704,6 +715,7 @@ int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t 
       rc = fail(MF_ERR_OOM, "host allocation");
     } else {
       e = cudaMemcpy(h, tr, (size_t)nr * sizeof(int2), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && trn) e = cudaMemcpy(round_ns, trn, (size_t)nr * sizeof(int), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) rc = cuda_fail(e, "trace copy");
       for (long long k = 0; k < nr && rc == MF_OK; k++) {
         live[k] = h[k].x;
@@ -713,7 +725,7 @@ int mf_solve_trace(mf_graph *g, int32_t *live, int32_t *relabel_before, int64_t 
     }
   }
   if (rounds && rc == MF_OK) *rounds = g->h_ctl->rounds;
-  if (tr) cudaFree(tr);
+  release();
   return rc;
 }
 

@@ -159,8 +159,10 @@ struct Dev {
                            // every vertex other than a source or sink is thread-sized (one thread per vertex)
   // per-round trace (nullable): trace[k] = {list entries of round k, 1 if a global relabel ran just before}
   int2 *trace;
+  int *trace_ns;          // nullable: ns of round k (CTA 0: from its start to the end of its grid barrier)
   long long trace_cap;
   int *trace_lv;          // nullable: frontier size of every BFS level, in order
+  int *trace_lv_ns;       // nullable: ns of every BFS level (CTA 0, to the end of its grid barrier)
   long long trace_lv_cap;
   // outputs (device pointers, each nullable)
   long long *out_value;   // per instance

@@ -1526,6 +1526,16 @@ static __device__ void bfs_pull_level(const Dev &D, Shared &sh, int gen, int dep
   phase_end(D, sh, next, 0, nullptr);
 }
 
+// CTA 0 thread 0 after the grid barrier that ends a BFS level which started at
+// t0 and whose own expansion ended at t1 (%globaltimer): counters and trace.
+__device__ __forceinline__ void level_done(const Dev &D, unsigned long long t0, unsigned long long t1) {
+  const unsigned long long t2 = gtimer();
+  const long long k = D.ctl->levels++;
+  if (D.trace_lv_ns && k < D.trace_lv_cap) D.trace_lv_ns[k] = (int)min(t2 - t0, (unsigned long long)INT_MAX);
+  D.ctl->t_lwork += t1 - t0;
+  D.ctl->t_lwait += t2 - t1;
+}
+
 // Level 0 of a BFS from one seed with many arcs (slots [b, e)), the seed
 // labelled 0 and not queued (generation gen is empty): the whole grid offers
 // label 1 along its arcs, one arc per thread, into generation gen + 1. Ends
@@ -1549,11 +1559,7 @@ static __device__ __noinline__ bool bfs_wide_level(const Dev &D, Shared &sh, int
   phase_end(D, sh, gen + 1, 0, nullptr);
   const unsigned long long t1 = timer ? gtimer() : 0;
   if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
-  if (timer) {
-    D.ctl->levels++;
-    D.ctl->t_lwork += t1 - t0;
-    D.ctl->t_lwait += gtimer() - t1;
-  }
+  if (timer) level_done(D, t0, t1);
   return true;
 }
 
@@ -1635,11 +1641,7 @@ __device__ bool bfs(const Dev &D, Shared &sh, const int *seeds, const int *block
     const unsigned long long t1 = timer ? gtimer() : 0;
     if (!grid_sync(D, sh, where, PF_LEVEL, gen + 1)) return false;
     gen++;
-    if (timer) {
-      D.ctl->levels++;
-      D.ctl->t_lwork += t1 - t0;
-      D.ctl->t_lwait += gtimer() - t1;
-    }
+    if (timer) level_done(D, t0, t1);
   }
   return true;
 }
@@ -1861,6 +1863,7 @@ __device__ bool run_phase(const Dev &D, Shared &sh, const int *sinks, const int 
       const unsigned long long t3 = gtimer();
       D.ctl->t_dis += t3 - t0;
       D.ctl->t_rwait += t3 - tp;
+      if (D.trace_ns && rnd < D.trace_cap) D.trace_ns[rnd] = (int)min(t3 - t0, (unsigned long long)INT_MAX);
     }
     since_gr += sh.snap.work[rnd % 3];
     time_req = sh.snap.gr_req[rnd & 1] != 0;
@@ -2102,6 +2105,7 @@ __device__ bool run_union(const Dev &D, Shared &sh, int &r, int &gen, long long 
       const unsigned long long t3 = gtimer();
       D.ctl->t_dis += t3 - t0;
       D.ctl->t_rwait += t3 - tp;
+      if (D.trace_ns && rnd < D.trace_cap) D.trace_ns[rnd] = (int)min(t3 - t0, (unsigned long long)INT_MAX);
     }
     r++;
     gen++;

@@ -113,7 +113,7 @@ def lib():
         L.mf_solve_device.argtypes = [vp, vp, vp, vp, vp]
         L.mf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.mf_run_rounds.argtypes = [vp, i64, i32, vp, vp, vp, vp]
-        L.mf_solve_trace.argtypes = [vp, vp, vp, i64, vp, vp, i64, vp]
+        L.mf_solve_trace.argtypes = [vp, vp, vp, i64, vp, vp, i64, vp, vp, vp]
         L.mf_destroy_graph.argtypes = [vp]
         L.mf_destroy_graph.restype = None
         L.mf_batch_create.argtypes = [i32, vp, ctypes.POINTER(Options), ctypes.POINTER(vp)]
@@ -289,16 +289,21 @@ class Graph:
         """Outputs into torch CUDA tensors (int64[1], int32[m], int32/uint32[ceil(n/32)]), each optional."""
         _check(lib().mf_solve_device(self._h, _stream_ptr(stream), _ptr(value), _ptr(flow), _ptr(cut_bits)))
 
-    def solve_trace(self, capacity: int = 1 << 22, level_capacity: int = 1 << 22):
-        """One traced solve: (live int32[rounds], relabel int32[rounds], bfs frontier sizes int32[levels])."""
+    def solve_trace(self, capacity: int = 1 << 22, level_capacity: int = 1 << 22, times: bool = False):
+        """One traced solve: (live int32[rounds], relabel int32[rounds], bfs frontier sizes int32[levels]), and
+        with times=True also the durations in ns of every round and every BFS level (int32 each)."""
         live = np.zeros(capacity, np.int32)
         gr = np.zeros(capacity, np.int32)
         lv = np.zeros(level_capacity, np.int32)
+        rns = np.zeros(capacity, np.int32) if times else None
+        lns = np.zeros(level_capacity, np.int32) if times else None
         nr, nl = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().mf_solve_trace(self._h, _ptr(live), _ptr(gr), capacity, ctypes.byref(nr), _ptr(lv),
-                                    level_capacity, ctypes.byref(nl)))
+                                    level_capacity, ctypes.byref(nl), _ptr(rns), _ptr(lns)))
         k = min(int(nr.value), capacity)
         kl = min(int(nl.value), level_capacity)
+        if times:
+            return live[:k], gr[:k], lv[:kl], rns[:k], lns[:kl]
         return live[:k], gr[:k], lv[:kl]
 
     def stats(self) -> dict:

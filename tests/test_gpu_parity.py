@@ -267,9 +267,12 @@ def test_trace_matches_stats(gpu, hops):
     csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
     # (bottom-up levels count the vertices they reach, not the frontier: off here)
     with gpu.Graph.from_csr(csr, g.s, g.t, gpu.default_options(bfs_hops=hops, bfs_pull=0)) as G:
-        live, gr, levels = G.solve_trace()
+        live, gr, levels, rns, lns = G.solve_trace(times=True)
         st = G.stats()
     assert len(live) == st["rounds"] and len(levels) == st["bfs_levels"]
+    # durations: every round and level took some time, and together no more than the solve
+    assert (rns > 0).all() and (lns > 0).all()
+    assert (int(rns.sum()) + int(lns.sum())) * 1e-6 <= st["solve_ms"] * 1.01 + 0.05
     assert gr[0] == 1 and int(gr.sum()) <= st["global_relabels"]
     assert (live > 0).all()
     if hops == 1:
