@@ -496,7 +496,7 @@ def serve_section(args) -> dict:
         return c, (g.s, g.t)
 
     budget = 64 << 30
-    sopt = apply_overrides(mf.default_options(device=0), args)
+    sopt = apply_overrides(mf.service_default_options(device=0), args)
     jobs = host_jobs()
     # saturated throughput on the prefix
     feeder = Feeder(make, P, jobs, 4 * jobs)
@@ -526,7 +526,8 @@ def serve_section(args) -> dict:
                        "checked_saturated": chk0["checked"], "matched_saturated": chk0["matched"],
                        "golden": "tests/golden/serving_stream_1000.json" if gold else None},
             "latency": "submission to completion, measured by the service (mf_wait)",
-            "options": args.options or "defaults"}
+            "options": "service defaults (mf_service_default_options: lanes of 128-thread CTAs)"
+                       + (f", overridden by {args.options}" if args.options else "")}
 
 
 def run_batch(args):

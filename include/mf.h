@@ -381,6 +381,11 @@ int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, d
  * queued requests.
  */
 int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_service **out);
+/* The options mf_service_create uses when opt is NULL: mf_default_options
+ * with block_threads 128, i.e. four lanes on a GB300 (with 256 threads two
+ * lanes fit; on the serving stream four lanes halved the median latency of the
+ * small requests at the same throughput). */
+void mf_service_default_options(mf_options *o);
 int mf_submit(mf_service *svc, const mf_graph_desc *g, mf_ticket *out);
 int mf_poll(mf_service *svc, mf_ticket ticket, int64_t *flow_value, int32_t *arc_flow, uint32_t *cut_bits);
 int mf_wait(mf_service *svc, mf_ticket ticket, int32_t timeout_ms, double *latency_ms);

@@ -513,6 +513,14 @@ void mf_default_options(mf_options *o) {
   o->instance_relabel = 1;
 }
 
+void mf_service_default_options(mf_options *o) {
+  if (!o) return;
+  mf_default_options(o);
+  // lanes of 128-thread CTAs: four lanes' persistent launches fit the SMs together (two with 256 threads),
+  // so a request that arrives while others are solving finds a free lane sooner
+  o->block_threads = 128;
+}
+
 const char *mf_last_error(void) { return last_error(); }
 
 void mf_struct_sizes(int32_t *options_bytes, int32_t *stats_bytes) {

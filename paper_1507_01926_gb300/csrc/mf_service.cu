@@ -212,7 +212,7 @@ int mf_service_create(size_t device_budget_bytes, const mf_options *opt, mf_serv
   if (opt)
     o = *opt;
   else
-    mf_default_options(&o);
+    mf_service_default_options(&o);
   int rc = check_options(&o);
   if (rc) return rc;
   cudaError_t e = cudaSetDevice(o.device);

@@ -74,7 +74,7 @@ class GraphDesc(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["mf_default_options", "mf_struct_sizes", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
+EXPORTS = ["mf_default_options", "mf_service_default_options", "mf_struct_sizes", "mf_last_error", "mf_build_csr", "mf_free_csr", "mf_create_graph",
            "mf_create_graph_device", "mf_solve", "mf_solve_device", "mf_get_stats", "mf_run_rounds",
            "mf_solve_trace", "mf_destroy_graph", "mf_batch_create", "mf_batch_solve", "mf_batch_get_stats",
            "mf_batch_destroy", "mf_service_create", "mf_submit", "mf_poll", "mf_wait", "mf_service_destroy",
@@ -101,6 +101,8 @@ def lib():
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         L.mf_default_options.argtypes = [ctypes.POINTER(Options)]
         L.mf_default_options.restype = None
+        L.mf_service_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.mf_service_default_options.restype = None
         L.mf_last_error.restype = ctypes.c_char_p
         L.mf_build_csr.argtypes = [i32, i64, vp, vp, vp, ctypes.POINTER(_CSR)]
         L.mf_free_csr.argtypes = [ctypes.POINTER(_CSR)]
@@ -167,6 +169,17 @@ def _stream_ptr(stream):
 def default_options(**overrides) -> Options:
     o = Options()
     lib().mf_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def service_default_options(**overrides) -> Options:
+    """mf_service_default_options (what mf_service_create uses without options), with overrides."""
+    o = Options()
+    lib().mf_service_default_options(ctypes.byref(o))
     for k, v in overrides.items():
         if not hasattr(o, k):
             raise KeyError(k)

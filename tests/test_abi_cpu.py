@@ -35,6 +35,9 @@ def test_default_options(built):
     o = mf.default_options()
     assert o.gr_freq == 0.5 and o.gr_alpha == 6 and o.work_beta == 12
     assert o.block_threads % 32 == 0 and o.timeout_ms > 0
+    so = mf.service_default_options()
+    assert so.block_threads == 128
+    assert all(getattr(so, k) == getattr(o, k) for k, _ in mf.Options._fields_ if k != "block_threads")
 
 
 def check_csr(c, tail, head, cap):
