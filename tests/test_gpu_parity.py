@@ -206,6 +206,24 @@ def test_global_relabel_labels_exact(gpu, rounds, which):
     assert np.array_equal(lab, d), f"{int((lab != d).sum())} labels differ"
 
 
+@pytest.mark.parametrize("opts", [dict(local_lists=0, bfs_pull=50), dict(local_lists=0, bfs_pull=0),
+                                  dict(bfs_hops=1), dict(bfs_hops=8)])
+def test_wide_seed_level_labels_and_cut(gpu, opts):
+    """The sink of this grid has 528 arcs, more than a CTA of 128 threads: the first level of every BFS from it
+    (and of the cut BFS from s) is expanded by the whole grid, and the level loop starts at depth 1. With
+    level-synchronous levels (top-down, bottom-up) and label-correcting ones the labels after a global
+    relabel must be the oracle's BFS distances, and the solve must give the oracle's value and S_min."""
+    g = I.grid3d(24, 22, 10, seed=14)
+    csr = gpu.build_csr(g.n, g.tail, g.head, g.cap)
+    o = gpu.default_options(block_threads=128, **opts)
+    for rounds in (0, 7):
+        with gpu.Graph.from_csr(csr, g.s, g.t, o) as G:
+            res, lab, _, _ = G.run_rounds(rounds, final_relabel=True)
+        rt, rh = residual_arcs(csr, res)
+        assert np.array_equal(lab, oracle.sink_distances(g.n, g.s, g.t, rt, rh))
+    solve_and_compare(gpu, g, o)
+
+
 @pytest.mark.parametrize("rounds", [1, 3, 10, 40])
 def test_preflow_invariants_mid_solve(gpu, rounds):
     """After any number of rounds: residuals in range, pair sums preserved, and every excess equals the net
