@@ -363,9 +363,10 @@ int mf_batch_autotune(mf_batch *b, const mf_tune_spec *spec, mf_options *best, d
  * that is set). mf_submit copies the instance (host arrays, paired-slot CSR)
  * and returns a ticket at once; MF_ERR_OVER_BUDGET if the instance alone would
  * exceed device_budget_bytes (its estimated device footprint is 77 bytes per
- * vertex + 32 bytes per slot). Lanes admit queued requests in arrival order
- * while the resident footprint stays within the budget and solve each admitted
- * group in one persistent launch. With instance_relabel (the default) every
+ * vertex + 32 bytes per slot). A free lane admits queued requests in arrival
+ * order, at most its share of the queue (queue length / lanes, rounded up),
+ * while the resident footprint stays within the budget, and solves each
+ * admitted group in one persistent launch. With instance_relabel (the default) every
  * request goes through its own phases inside the launch and is complete as soon
  * as its own results are written: the kernel flags it in mapped host memory,
  * the lane copies its outputs while the rest of the group is still solving,

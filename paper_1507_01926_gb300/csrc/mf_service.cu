@@ -142,8 +142,12 @@ static void lane_main(mf_service *svc, int lane) {
       });
       if (svc->stop) break;
       long long nn = 0, mm = 0;
+      // a lane takes its share of the queue (the rest is left to the other lanes, which run beside it), so
+      // that a burst is spread over all lanes instead of filling one lane's launch
+      const size_t share = (svc->pending.size() + (size_t)svc->lanes - 1) / (size_t)svc->lanes;
       while (!svc->pending.empty()) {
         if (o.union_max_requests > 0 && (int)batch.size() >= o.union_max_requests) break;
+        if (batch.size() >= share) break;
         Request *r = svc->pending.front();
         if (svc->in_use + bytes + r->bytes > svc->budget) break;
         if (svc->resident_n + nn + r->n > UNV - 4 || svc->resident_m + mm + r->m > 2147483646LL) break;
