@@ -58,7 +58,7 @@ const double kTimeRatio[] = {0.0, 1.0, 2.0, 4.0};
 const double kFreq[] = {0.25, 0.5, 1.0, 2.0};
 const int kBinThread[] = {2, 4, 8, 16};
 const int kBinWarp[] = {128, 1024, 8192};
-const int kShape[][2] = {{256, 2}, {512, 1}, {128, 4}, {256, 1}};  // threads per CTA, CTAs per SM
+const int kShape[][2] = {{256, 2}, {512, 1}, {128, 4}, {256, 1}, {64, 4}};  // threads per CTA, CTAs per SM
 // kernel_variant, with the bin_thread it is tried with (-1: unchanged); variant
 // 4's 16-slot thread path is tried together with bin_thread 16, which no other
 // variant accepts (one coordinate at a time could not reach the pair)
@@ -73,7 +73,7 @@ int candidates(Coord c) {
     case GR_FREQ: return 4;
     case BIN_THREAD: return 4;
     case BIN_WARP: return 3;
-    case SHAPE: return 4;
+    case SHAPE: return 5;
     case VARIANT: return 6;
     case LOCAL: return 2;
     case HOPS: return 4;

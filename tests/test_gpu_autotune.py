@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 CANDIDATES = {"gr_time_ratio": {0.0, 1.0, 2.0, 4.0}, "gr_freq": {0.25, 0.5, 1.0, 2.0}, "bin_thread": {2, 4, 8, 16},
               "bin_warp": {128, 1024, 8192}, "kernel_variant": {0, 1, 2, 3, 4}, "local_lists": {0, 1},
               "bfs_hops": {1, 4, 8, 16}, "bfs_pull": {0, 20, 50, 200}}
-SHAPES = {(256, 2), (512, 1), (128, 4), (256, 1)}
+SHAPES = {(256, 2), (512, 1), (128, 4), (256, 1), (64, 4)}
 
 
 def check_solution(mf, g, csr, r):
