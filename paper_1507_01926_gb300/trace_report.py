@@ -3,9 +3,9 @@
 Every push-relabel round and every BFS level ends with a grid barrier, so a solve is a sequence of short
 phases whose cost depends on how many vertices they touch. `breakdown` sums the phase durations CTA 0
 recorded into buckets of working-set (round) or frontier (BFS level) size; the command line runs it on the
-256x256x128 3D grid with the options the bench uses (GPU required):
+256x256x128 3D grid with the options the bench uses, or another grid (GPU required):
 
-    python -m paper_1507_01926_gb300.trace_report
+    python -m paper_1507_01926_gb300.trace_report [--solves K] [--grid3d X Y Z]
 """
 from __future__ import annotations
 
@@ -47,10 +47,12 @@ def main(argv=None) -> int:
 
     from . import autotune, inputs, mf
 
-    ap = argparse.ArgumentParser(description="Traced solve of the 256x256x128 3D grid, split by working-set size")
+    ap = argparse.ArgumentParser(description="Traced solve of a 3D grid, split by working-set size")
     ap.add_argument("--solves", type=int, default=1, help="traced solves (one JSON line each)")
+    ap.add_argument("--grid3d", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
+                    help="another grid than the 256x256x128 bench workload (same generator, seed 1)")
     a = ap.parse_args(argv)
-    g = inputs.grid3d_256x256x128()
+    g = inputs.grid3d(*a.grid3d, seed=1) if a.grid3d else inputs.grid3d_256x256x128()
     csr = mf.build_csr(g.n, g.tail, g.head, g.cap)
     hit = autotune.lookup(autotune.workload_key("grid3d", g.n, csr.m), autotune.device_name(0))
     opt = hit[0] if hit else mf.default_options()
