@@ -1,7 +1,7 @@
 #pragma once
-// The persistent solver kernel (included by mf_solver.cu, which instantiates it
-// for single graphs, and by mf_solver_multi.cu, which instantiates it for
-// batches and service unions; the two translation units compile in parallel).
+// The persistent solver kernel (instantiated by mf_kernels_s0.cu / _s1.cu for
+// single graphs and by mf_kernels_m0.cu / _m1.cu for batches and service
+// unions, units that compile in parallel; mf_solver.cu holds the launch code).
 //
 // Synchronous parallel push-relabel (arXiv:1507.01926, Section 3.1 and
 // Algorithm 1) with parallel global relabeling (Section 3, Algorithm 2) as one
